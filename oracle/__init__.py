@@ -1,0 +1,244 @@
+"""Parity oracle for stochastic multi-dimensional deconvolution (arXiv 2202.04486).
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, obviously correct FP64 CPU code written from the paper, used
+to check the CUDA path.  Only the tests, the smoke check and the benchmark's CPU-baseline / reference
+leg may import it.  It imports nothing from the CUDA package and shares no code with it.
+
+Tier A (the definition): direct time-domain convolution / cross-correlation sums in C
+(oracle/mdc_direct.c), for the forward operator P+_t of Eq. 3 restricted to a batch of sources
+(Eq. 5) and for its adjoint (the cross-correlation named in the Synthetic OBC section).
+
+Tier B: the same operator through numpy's FP64 FFT (Appendix A: FFT along time, one matrix product per
+frequency, inverse FFT), with zero padding to nfft >= 2 nt - 1 so that the circular convolution equals
+the causal linear one on [0, nt).  It is pinned to Tier A in the tests and used only where Tier A is
+too slow (multi-epoch trajectories).
+
+Pins (tests/test_oracle_pins.py): the 1D case against numpy.convolve / numpy.correlate, a delta
+down-going field, a dense operator built from scipy Toeplitz blocks, the adjoint dot-product test, the
+finite-sum identity of Eq. 5/6, the Landweber toy of Eq. 11 (sigma^2 = 53.0256), the spectral bound on
+the operator norm, and SGD converging to the least-squares solution of a tiny consistent problem.
+
+Readings of the paper taken here (each is also listed in the design notes):
+  * scale: the receiver integral of Eq. 1 is a plain sum over receivers times `scale` (default 1).
+  * gradient: g_B = P_B^H (P_B X - U_B), summed (not averaged) over the batch; the update is
+    X <- X - alpha * C(g_B) (Eq. 6 with its leading minus folded into the residual).
+  * reciprocity preconditioner C_r: 1/2 (G + G^T) with T swapping receiver and virtual source.
+  * steps per epoch: ceil(ns / nb), the last batch partial.
+  * RMSE (Eq. 7): plain L2 norm of the difference of the max-normalised fields.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        for name in ("oracle_mdc_forward", "oracle_mdc_adjoint"):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = [ctypes.c_int] * 4 + [dp, dp, ip, ctypes.c_int, ip, ctypes.c_int,
+                                                ctypes.c_double, dp]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the direct sums use."""
+    return int(_load().oracle_num_threads())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+# ----------------------------------------------------------------------------------------------
+# Tier A: direct sums
+# ----------------------------------------------------------------------------------------------
+def mdc_forward(D, X, idx, scale: float = 1.0, vsel=None) -> np.ndarray:
+    """Forward MDC for the sources idx (Eq. 1-3 in the time domain, batch form of Eq. 5).
+
+    U[b, j, t] = scale * sum_r sum_{tau<=t} D[idx[b], r, tau] * X[vsel[j], r, t - tau].
+    D: (ns, nr, nt), X: (nv, nr, nt) -> U: (nb, len(vsel), nt).  vsel defaults to all virtual sources.
+    """
+    D, X = _f64(D), _f64(X)
+    ns, nr, nt = D.shape
+    nv = X.shape[0]
+    assert X.shape == (nv, nr, nt)
+    idx = _i32(idx)
+    vsel = _i32(np.arange(nv) if vsel is None else vsel)
+    U = np.zeros((idx.size, vsel.size, nt))
+    rc = _load().oracle_mdc_forward(nt, nr, nv, ns, _ptr(D, ctypes.c_double), _ptr(X, ctypes.c_double),
+                                    _ptr(idx, ctypes.c_int32), idx.size, _ptr(vsel, ctypes.c_int32),
+                                    vsel.size, float(scale), _ptr(U, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_mdc_forward: invalid argument")
+    return U
+
+
+def mdc_adjoint(D, R, idx, scale: float = 1.0, vsel=None) -> np.ndarray:
+    """Adjoint MDC: cross-correlation of the residual with the down-going field (Eq. 6).
+
+    G[j, r, tau] = scale * sum_b sum_{t>=tau} D[idx[b], r, t - tau] * R[b, vsel[j], t].
+    D: (ns, nr, nt), R: (nb, nv, nt) -> G: (len(vsel), nr, nt).
+    """
+    D, R = _f64(D), _f64(R)
+    ns, nr, nt = D.shape
+    nb, nv, _ = R.shape
+    idx = _i32(idx)
+    assert idx.size == nb and R.shape[2] == nt
+    vsel = _i32(np.arange(nv) if vsel is None else vsel)
+    G = np.zeros((vsel.size, nr, nt))
+    rc = _load().oracle_mdc_adjoint(nt, nr, nv, ns, _ptr(D, ctypes.c_double), _ptr(R, ctypes.c_double),
+                                    _ptr(idx, ctypes.c_int32), nb, _ptr(vsel, ctypes.c_int32),
+                                    vsel.size, float(scale), _ptr(G, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_mdc_adjoint: invalid argument")
+    return G
+
+
+# ----------------------------------------------------------------------------------------------
+# Tier B: the same operator through the FFT (Appendix A), numpy FP64
+# ----------------------------------------------------------------------------------------------
+def default_nfft(nt: int) -> int:
+    """Smallest power of two >= 2 nt - 1 (linear, not circular, convolution on [0, nt))."""
+    n = 1
+    while n < 2 * nt - 1:
+        n *= 2
+    return n
+
+
+def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None) -> np.ndarray:
+    """Tier B forward: rfft along time, per-frequency matrix product, irfft, keep t < nt."""
+    D, X = _f64(D), _f64(X)
+    nt = D.shape[2]
+    nfft = nfft or default_nfft(nt)
+    assert nfft >= 2 * nt - 1
+    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
+    Xh = np.fft.rfft(X, n=nfft, axis=-1)                            # (nv, nr, nf)
+    Uh = np.einsum("brf,vrf->bvf", Dh, Xh)
+    return scale * np.fft.irfft(Uh, n=nfft, axis=-1)[..., :nt]
+
+
+def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None) -> np.ndarray:
+    """Tier B adjoint: spectra of the residual times the conjugate down-going spectra, summed over the batch."""
+    D, R = _f64(D), _f64(R)
+    nt = D.shape[2]
+    nfft = nfft or default_nfft(nt)
+    assert nfft >= 2 * nt - 1
+    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
+    Rh = np.fft.rfft(R, n=nfft, axis=-1)                            # (nb, nv, nf)
+    Gh = np.einsum("bvf,brf->vrf", Rh, np.conj(Dh))
+    return scale * np.fft.irfft(Gh, n=nfft, axis=-1)[..., :nt]
+
+
+# ----------------------------------------------------------------------------------------------
+# Stochastic MDD step (Eq. 5-6) and helpers
+# ----------------------------------------------------------------------------------------------
+def reciprocity(G) -> np.ndarray:
+    """Reciprocity preconditioner C_r (Eq. 4): 1/2 (G + G^T), T swapping receiver and virtual source."""
+    G = _f64(G)
+    assert G.shape[0] == G.shape[1], "reciprocity needs nr == nv"
+    return 0.5 * (G + G.transpose(1, 0, 2))
+
+
+def loss(R) -> float:
+    """1/2 ||R||^2 of the batch residual (the summand of Eq. 5 over the batch)."""
+    R = _f64(R)
+    return 0.5 * float(np.sum(R * R))
+
+
+def gradient(D, X, U_obs, idx, scale: float = 1.0, fft: bool = False):
+    """Mini-batch gradient of Eq. 6: g_B = P_B^H (P_B X - U_obs[idx]).  Returns (g, loss, residual)."""
+    idx = np.asarray(idx)
+    fwd = mdc_forward_fft if fft else mdc_forward
+    adj = mdc_adjoint_fft if fft else mdc_adjoint
+    R = fwd(D, X, idx, scale) - _f64(U_obs)[idx]
+    return adj(D, R, idx, scale), loss(R), R
+
+
+def sgd_step(D, X, U_obs, idx, alpha: float, *, recip: bool = False, scale: float = 1.0,
+             fft: bool = False):
+    """One stochastic MDD step (SGD): X <- X - alpha * C(g_B), C = C_r or identity.  Returns (X_new, loss)."""
+    g, l, _ = gradient(D, X, U_obs, idx, scale, fft)
+    if recip:
+        g = reciprocity(g)
+    return _f64(X) - alpha * g, l
+
+
+def run_epochs(D, X0, U_obs, batches, alpha: float, *, recip: bool = False, scale: float = 1.0,
+               fft: bool = False):
+    """Run the given epochs of batches (batches[epoch][step] -> source indices).  Returns (X, losses)."""
+    X = _f64(X0).copy()
+    losses = []
+    for epoch in batches:
+        for idx in epoch:
+            X, l = sgd_step(D, X, U_obs, idx, alpha, recip=recip, scale=scale, fft=fft)
+            losses.append(l)
+    return X, losses
+
+
+def steps_per_epoch(ns: int, nb: int) -> int:
+    """Number of batches in one epoch: ceil(ns / nb) (the last batch is partial)."""
+    return -(-ns // nb)
+
+
+def sigma2_max(D, nfft: int | None = None, scale: float = 1.0) -> float:
+    """Largest squared singular value of the kernel over frequencies (Appendix B):
+    max_f lambda_max(Dh_f^H Dh_f), Dh_f = unnormalised DFT of D along time at bin f, as an ns x nr matrix.
+    This bounds sigma^2 of the time-domain operator from above (it is the norm of its circulant embedding)."""
+    D = _f64(D)
+    nt = D.shape[2]
+    nfft = nfft or default_nfft(nt)
+    Dh = np.fft.rfft(D, n=nfft, axis=-1)                            # (ns, nr, nf)
+    s = np.linalg.svd(np.moveaxis(Dh, -1, 0), compute_uv=False)     # (nf, min(ns,nr))
+    return float(scale * scale * np.max(s[:, 0] ** 2))
+
+
+def landweber_alpha(sigma2: float, kappa: float) -> float:
+    """Step size kappa * 2 / sigma^2 (Appendix B; kappa < 1 is inside the Landweber bound)."""
+    return kappa * 2.0 / sigma2
+
+
+def landweber(A, y, alpha: float, n_iter: int, x0=None) -> np.ndarray:
+    """Landweber iteration x <- x + alpha A^T (y - A x) on a dense matrix (Appendix B, Eq. 11).
+    Returns the iterates, shape (n_iter + 1, n)."""
+    A, y = _f64(A), _f64(y)
+    x = np.zeros(A.shape[1]) if x0 is None else _f64(x0).copy()
+    out = [x.copy()]
+    for _ in range(n_iter):
+        x = x + alpha * (A.T @ (y - A @ x))
+        out.append(x.copy())
+    return np.array(out)
+
+
+def rmse(x_true, x_est) -> float:
+    """Eq. 7 as read here: || x_true / max|x_true| - x_est / max|x_est| ||_2 (plain L2 norm)."""
+    a, b = _f64(x_true), _f64(x_est)
+    return float(np.linalg.norm(a / np.max(np.abs(a)) - b / np.max(np.abs(b))))
+
+
+def rel_l2(a, ref) -> float:
+    """||a - ref|| / ||ref|| in FP64."""
+    a, ref = _f64(a), _f64(ref)
+    return float(np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-300))

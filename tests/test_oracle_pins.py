@@ -1,0 +1,293 @@
+"""Pins for the FP64 oracle: each check is fixed by the paper or by mathematics, not by the oracle itself.
+
+A plausible mistake in the oracle (a dropped term, a sign, a transposed operand, an off-by-one in the
+causal window or in the correlation lag, a wrong source index) fails at least one of these.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from paper_2202_04486_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense_operator(D, idx, nv, scale=1.0):
+    """Dense matrix of the batch MDC built from scipy Toeplitz blocks (independent of the oracle's loops).
+
+    Rows: (b, v, t) of U; columns: (v', r, tau) of X.  Block (b, v; v', r) = delta_{v v'} * T(D[idx_b, r]),
+    T(d) the lower-triangular Toeplitz matrix with first column d (causal convolution, truncated)."""
+    ns, nr, nt = D.shape
+    nb = len(idx)
+    A = np.zeros((nb * nv * nt, nv * nr * nt))
+    for b, s in enumerate(idx):
+        for r in range(nr):
+            T = scipy.linalg.toeplitz(D[s, r], np.zeros(nt))
+            for v in range(nv):
+                A[(b * nv + v) * nt:(b * nv + v + 1) * nt, (v * nr + r) * nt:(v * nr + r + 1) * nt] = scale * T
+    return A
+
+
+# ------------------------------------------------------------------------------------------ 1D case
+@pytest.mark.parametrize("nt", [1, 2, 7, 33])
+def test_1d_forward_is_numpy_convolve(nt):
+    d = synth.random_traces((1, 1, nt), seed=nt)
+    x = synth.random_traces((1, 1, nt), seed=100 + nt)
+    U = oracle.mdc_forward(d, x, [0])
+    np.testing.assert_allclose(U[0, 0], np.convolve(d[0, 0], x[0, 0])[:nt], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("nt", [1, 2, 7, 33])
+def test_1d_adjoint_is_numpy_correlate(nt):
+    d = synth.random_traces((1, 1, nt), seed=nt)
+    r = synth.random_traces((1, 1, nt), seed=200 + nt)
+    G = oracle.mdc_adjoint(d, r, [0])
+    # correlate(r, d, 'full')[nt-1+tau] = sum_t r[t+tau] d[t]  ->  G[tau] = sum_t d[t-tau] r[t]
+    ref = np.correlate(r[0, 0], d[0, 0], mode="full")[nt - 1:]
+    np.testing.assert_allclose(G[0, 0], ref, rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------------------------------------------ delta kernel
+@pytest.mark.parametrize("k", [0, 1, 5])
+def test_delta_kernel_shifts_model(k):
+    """D[s, r, t] = delta_{sr} delta_{t,k}: U[b, v, t] = X[v, idx_b, t - k] (zero filled, truncated)."""
+    n, nt, nv = 5, 12, 3
+    D = np.zeros((n, n, nt))
+    for s in range(n):
+        D[s, s, k] = 1.0
+    X = synth.random_traces((nv, n, nt), seed=3)
+    idx = np.array([4, 0, 2, 2])
+    U = oracle.mdc_forward(D, X, idx)
+    ref = np.zeros_like(U)
+    for b, s in enumerate(idx):
+        ref[b, :, k:] = X[:, s, :nt - k]
+    np.testing.assert_array_equal(U, ref)
+    # and the adjoint moves the residual back by k into receiver idx_b
+    R = synth.random_traces((len(idx), nv, nt), seed=4)
+    G = oracle.mdc_adjoint(D, R, idx)
+    refG = np.zeros((nv, n, nt))
+    for b, s in enumerate(idx):
+        refG[:, s, :nt - k] += R[b, :, k:]
+    np.testing.assert_allclose(G, refG, rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------ brute force
+@pytest.mark.parametrize("shape", [(1, 2, 1, 3, 2), (4, 2, 3, 3, 3), (6, 3, 2, 4, 2), (5, 2, 2, 2, 4)])
+def test_dense_operator_brute_force(shape):
+    nt, nr, nv, ns, nb = shape
+    D = synth.random_traces((ns, nr, nt), seed=11)
+    X = synth.random_traces((nv, nr, nt), seed=12)
+    R = synth.random_traces((nb, nv, nt), seed=13)
+    idx = synth.random_indices(ns, nb, seed=14, replace=True)
+    A = _dense_operator(D, idx, nv, scale=0.7)
+    U = oracle.mdc_forward(D, X, idx, scale=0.7)
+    np.testing.assert_allclose(U.ravel(), A @ X.ravel(), rtol=1e-12, atol=1e-12)
+    G = oracle.mdc_adjoint(D, R, idx, scale=0.7)
+    np.testing.assert_allclose(G.ravel(), A.T @ R.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_virtual_source_selection_matches_full():
+    D = synth.random_traces((6, 4, 9), seed=1)
+    X = synth.random_traces((5, 4, 9), seed=2)
+    R = synth.random_traces((3, 5, 9), seed=3)
+    idx = np.array([5, 1, 3])
+    vsel = np.array([4, 0, 2])
+    np.testing.assert_array_equal(oracle.mdc_forward(D, X, idx, vsel=vsel), oracle.mdc_forward(D, X, idx)[:, vsel])
+    np.testing.assert_array_equal(oracle.mdc_adjoint(D, R, idx, vsel=vsel), oracle.mdc_adjoint(D, R, idx)[vsel])
+
+
+def test_invalid_index_rejected():
+    D = np.zeros((3, 2, 4))
+    X = np.zeros((2, 2, 4))
+    with pytest.raises(ValueError):
+        oracle.mdc_forward(D, X, [3])
+    with pytest.raises(ValueError):
+        oracle.mdc_adjoint(D, np.zeros((1, 2, 4)), [-1])
+
+
+# ------------------------------------------------------------------------------------------ dot test
+@pytest.mark.parametrize("shape", [(16, 5, 4, 7, 3), (37, 3, 6, 5, 5)])
+def test_adjoint_dot_product(shape):
+    nt, nr, nv, ns, nb = shape
+    D = synth.random_traces((ns, nr, nt), seed=21)
+    X = synth.random_traces((nv, nr, nt), seed=22)
+    Y = synth.random_traces((nb, nv, nt), seed=23)
+    idx = synth.random_indices(ns, nb, seed=24)
+    lhs = np.vdot(oracle.mdc_forward(D, X, idx), Y)
+    rhs = np.vdot(X, oracle.mdc_adjoint(D, Y, idx))
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
+
+
+# ------------------------------------------------------------------------------------------ finite sum
+def test_finite_sum_identity():
+    """Eq. 5/6: the batch gradients over a partition of the sources add up to the full gradient."""
+    nt, nr, nv, ns, nb = 20, 4, 3, 11, 4
+    D = synth.random_traces((ns, nr, nt), seed=31)
+    X = synth.random_traces((nv, nr, nt), seed=32)
+    U = synth.random_traces((ns, nv, nt), seed=33)
+    g_full, l_full, _ = oracle.gradient(D, X, U, np.arange(ns))
+    batches = synth.epoch_batches(ns, nb, 1, seed=5)[0]
+    assert len(batches) == oracle.steps_per_epoch(ns, nb) == 3
+    parts = [oracle.gradient(D, X, U, b) for b in batches]
+    g_sum = sum(p[0] for p in parts)
+    l_sum = sum(p[1] for p in parts)
+    assert np.linalg.norm(g_sum - g_full) <= 1e-13 * np.linalg.norm(g_full)
+    assert abs(l_sum - l_full) <= 1e-13 * l_full
+    # duplicates count twice, exactly as in the sum of Eq. 6
+    g_dup, _, _ = oracle.gradient(D, X, U, [2, 2])
+    g_one, _, _ = oracle.gradient(D, X, U, [2])
+    np.testing.assert_allclose(g_dup, 2 * g_one, rtol=1e-14, atol=1e-14)
+
+
+def test_gradient_is_derivative_of_loss():
+    """g_B is the gradient of 1/2||P_B X - U_B||^2 (central differences; the loss is quadratic so they are exact)."""
+    nt, nr, nv, ns = 8, 3, 2, 4
+    D = synth.random_traces((ns, nr, nt), seed=41)
+    X = synth.random_traces((nv, nr, nt), seed=42)
+    U = synth.random_traces((ns, nv, nt), seed=43)
+    idx = [3, 1]
+    g, _, _ = oracle.gradient(D, X, U, idx)
+    E = synth.random_traces(X.shape, seed=44)
+    h = 1e-3
+    lp = oracle.gradient(D, X + h * E, U, idx)[1]
+    lm = oracle.gradient(D, X - h * E, U, idx)[1]
+    assert abs((lp - lm) / (2 * h) - np.vdot(g, E)) <= 1e-9 * max(1.0, abs(np.vdot(g, E)))
+
+
+# ------------------------------------------------------------------------------------------ Tier B
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1, 1), (13, 3, 4, 5, 2), (64, 6, 5, 7, 4), (100, 2, 3, 3, 3)])
+def test_tier_b_fft_matches_direct_sums(shape):
+    nt, nr, nv, ns, nb = shape
+    D = synth.random_traces((ns, nr, nt), seed=51)
+    X = synth.random_traces((nv, nr, nt), seed=52)
+    R = synth.random_traces((nb, nv, nt), seed=53)
+    idx = synth.random_indices(ns, nb, seed=54)
+    assert oracle.rel_l2(oracle.mdc_forward_fft(D, X, idx, 1.3), oracle.mdc_forward(D, X, idx, 1.3)) < 1e-12
+    assert oracle.rel_l2(oracle.mdc_adjoint_fft(D, R, idx, 1.3), oracle.mdc_adjoint(D, R, idx, 1.3)) < 1e-12
+
+
+def test_nfft_too_short_is_circular_and_rejected():
+    with pytest.raises(AssertionError):
+        oracle.mdc_forward_fft(np.zeros((1, 1, 8)), np.zeros((1, 1, 8)), [0], nfft=8)
+
+
+# ------------------------------------------------------------------------------------------ Landweber (App. B)
+def test_landweber_toy():
+    g = json.load(open(os.path.join(GOLDEN, "landweber_toy.json")))
+    A = np.array(g["A"], float)
+    x = np.array(g["x"], float)
+    s2 = np.linalg.norm(A, 2) ** 2
+    assert round(s2) == g["sigma2_printed"]
+    assert abs(s2 - (67 + math.sqrt(1525)) / 2) < 1e-12
+    y = A @ x
+    ok = oracle.landweber(A, y, g["bound_fraction_converges"] / s2, 400)
+    bad = oracle.landweber(A, y, g["bound_fraction_diverges"] / s2, 400)
+    assert np.linalg.norm(ok[-1] - x) < 1e-6
+    assert np.linalg.norm(bad[-1] - x) > 1e3
+    # the residual of the divergent run grows geometrically at the rate |1 - alpha sigma^2| = 1.05
+    e = [np.linalg.norm(it - x) for it in bad[-20:]]
+    assert 1.04 < (e[-1] / e[0]) ** (1 / 19) < 1.06
+
+
+def test_sigma2_bounds_operator_norm():
+    """sigma_max of the truncated time-domain operator <= max_f sigma_max(Dh_f) (its circulant embedding),
+    and the bound tightens as the record gets longer than the kernel support."""
+    rng_D = synth.random_traces((3, 2, 6), seed=61)
+    ratios = []
+    for nt in (6, 24, 96):
+        D = np.zeros((3, 2, nt))
+        D[:, :, :6] = rng_D
+        A = _dense_operator(D, [0, 1, 2], nv=1)
+        s2_op = np.linalg.norm(A, 2) ** 2
+        s2_k = oracle.sigma2_max(D)
+        assert s2_op <= s2_k * (1 + 1e-12)
+        ratios.append(s2_op / s2_k)
+    assert ratios[0] < ratios[1] < ratios[2] and ratios[2] > 0.95
+
+
+def test_sgd_full_batch_is_landweber_and_converges_to_lstsq():
+    """Full-batch SGD with alpha < 2/sigma^2 is the Landweber iteration; from 0 on a consistent system it
+    converges to the minimum-norm least-squares solution (numpy.linalg.lstsq on the dense operator)."""
+    nt, nr, nv, ns = 5, 2, 2, 4
+    D = synth.random_traces((ns, nr, nt), seed=71)
+    Xt = synth.random_traces((nv, nr, nt), seed=72)
+    U = oracle.mdc_forward(D, Xt, np.arange(ns))
+    A = _dense_operator(D, np.arange(ns), nv)
+    s2 = np.linalg.norm(A, 2) ** 2
+    X = np.zeros_like(Xt)
+    alpha = 1.9 / s2
+    for _ in range(4000):
+        X, _ = oracle.sgd_step(D, X, U, np.arange(ns), alpha)
+    x_ls = np.linalg.lstsq(A, U.ravel(), rcond=None)[0]
+    assert np.linalg.norm(X.ravel() - x_ls) < 1e-6 * np.linalg.norm(x_ls)
+
+
+def test_sgd_minibatch_converges_on_consistent_problem():
+    nt, nr, nv, ns, nb = 5, 2, 2, 6, 2
+    D = synth.random_traces((ns, nr, nt), seed=81)
+    Xt = synth.random_traces((nv, nr, nt), seed=82)
+    U = oracle.mdc_forward(D, Xt, np.arange(ns))
+    A = _dense_operator(D, np.arange(ns), nv)
+    alpha = 0.5 / (np.linalg.norm(A, 2) ** 2)
+    X, losses = oracle.run_epochs(D, np.zeros_like(Xt), U, synth.epoch_batches(ns, nb, 1500, seed=1), alpha)
+    x_ls = np.linalg.lstsq(A, U.ravel(), rcond=None)[0]
+    assert np.linalg.norm(X.ravel() - x_ls) < 1e-5 * np.linalg.norm(x_ls)
+    assert losses[-1] < 1e-12 * losses[0]
+
+
+# ------------------------------------------------------------------------------------------ reciprocity
+def test_reciprocity_keeps_model_symmetric():
+    n, nt, ns = 4, 10, 5
+    D = synth.random_traces((ns, n, nt), seed=91)
+    Xt = synth.random_traces((n, n, nt), seed=92)
+    Xt = Xt + Xt.transpose(1, 0, 2)
+    U = oracle.mdc_forward(D, Xt, np.arange(ns))
+    X = np.zeros_like(Xt)
+    for idx in synth.epoch_batches(ns, 2, 3, seed=2)[0]:
+        g, _, _ = oracle.gradient(D, X, U, idx)
+        Xn, _ = oracle.sgd_step(D, X, U, idx, 1e-3, recip=True)
+        np.testing.assert_array_equal(Xn, Xn.transpose(1, 0, 2))
+        np.testing.assert_allclose((X - Xn) / 1e-3, 0.5 * (g + g.transpose(1, 0, 2)), rtol=1e-9, atol=1e-12)
+        X = Xn
+
+
+def test_reciprocity_is_orthogonal_projection():
+    G = synth.random_traces((3, 3, 4), seed=93)
+    P = oracle.reciprocity(G)
+    np.testing.assert_allclose(oracle.reciprocity(P), P, rtol=0, atol=0)
+    H = synth.random_traces((3, 3, 4), seed=94)
+    assert abs(np.vdot(oracle.reciprocity(G), H) - np.vdot(G, oracle.reciprocity(H))) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------ epoch + metrics
+def test_steps_per_epoch_golden():
+    g = json.load(open(os.path.join(GOLDEN, "epoch_counts.json")))
+    for c in g["printed"] + g["reading_cases"]:
+        assert oracle.steps_per_epoch(c["ns"], c["nb"]) == c["steps"]
+        b = synth.epoch_batches(c["ns"], c["nb"], 2, seed=0)
+        assert all(len(e) == c["steps"] for e in b)
+        for e in b:
+            assert sorted(np.concatenate(e).tolist()) == list(range(c["ns"]))
+
+
+def test_rmse_reading():
+    x = synth.random_traces((3, 4, 5), seed=95)
+    assert oracle.rmse(x, x) == 0.0
+    assert oracle.rmse(x, 3.0 * x) < 1e-15
+    y = np.zeros_like(x)
+    y.flat[0] = 1.0
+    a = x / np.max(np.abs(x))
+    assert abs(oracle.rmse(x, y) - math.sqrt(np.sum((a - y) ** 2))) < 1e-14
+
+
+def test_generator_reciprocal_and_seeded():
+    p = synth.make_problem(64, 6, 6, 7, seed=3)
+    np.testing.assert_array_equal(p.X_true, p.X_true.transpose(1, 0, 2))
+    q = synth.make_problem(64, 6, 6, 7, seed=3)
+    np.testing.assert_array_equal(p.D, q.D)
+    assert np.max(np.abs(p.D)) > 0.5 and np.max(np.abs(p.X_true)) > 0.1
