@@ -1,0 +1,146 @@
+/*
+ * smdd.h -- C ABI of the GB300 (sm_103a) stochastic multi-dimensional deconvolution hot path.
+ *
+ * The operator is the time-domain multi-dimensional convolution (MDC) of Ravasi, Selvan & Luiken,
+ * "Stochastic Multi-Dimensional Deconvolution" (arXiv 2202.04486): Eq. 1-2 written in the time domain
+ * (the operator P+_t of Eq. 3), applied to a batch of sources (Eq. 5), its adjoint (the
+ * cross-correlation of the Synthetic OBC section), and one SGD step on the mini-batch gradient of
+ * Eq. 6 with the optional reciprocity preconditioner C_r of Eq. 4.  Appendix A gives the evaluation
+ * order used here: FFT along time, one complex matrix product per frequency, inverse FFT.
+ *
+ * Array conventions.  All arrays are float32, C order, time axis fastest:
+ *   D     [ns][nr][nt]  down-going wavefield p+ (source s, receiver r)
+ *   X     [nv][nr][nt]  reflection response r_t (virtual source v, receiver r)
+ *   U_obs [ns][nv][nt]  observed up-going wavefield p- (source s, virtual source v)
+ *   U     [nb][nv][nt]  MDC output for the sources idx[0..nb)
+ *   R     [nb][nv][nt]  residual / adjoint input for the sources idx[0..nb)
+ *   G     [nv][nr][nt]  adjoint output
+ * with
+ *   U[b][v][t] = scale * sum_r sum_{tau=0..t} D[idx[b]][r][tau] * X[v][r][t-tau]          (forward)
+ *   G[v][r][tau] = scale * sum_b sum_{t=tau..nt-1} D[idx[b]][r][t-tau] * R[b][v][t]       (adjoint)
+ * i.e. causal linear convolution truncated to the nt recorded samples (the FFT length nfft is at
+ * least 2*nt-1, so no circular wrap-around reaches [0, nt)).
+ *
+ * Memory and streams.  Every array pointer is DEVICE memory owned by the caller unless stated
+ * otherwise; the plan owns its own workspaces (spectrum of D, model/gradient spectra, batch spectra).
+ * Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is the legacy
+ * default stream).  A plan must not be used by two calls that may overlap on the GPU (its workspaces
+ * are shared); issue all calls on one plan to one stream, or order the streams.
+ *
+ * Errors.  Every call returns an mdc_status.  Host-detectable errors (null pointers, bad sizes,
+ * nb > nb_max, shape mismatch for reciprocity) are returned immediately and nothing is launched.
+ * Device-detected errors (a source index outside [0, ns)) are recorded in the plan's status word:
+ * the offending rows are treated as zero and the error is returned by mdc_plan_sync_status().
+ * Nothing traps and no C++ exception crosses this interface.
+ */
+#ifndef SMDD_H
+#define SMDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdc_plan_s *mdc_plan_t;
+
+typedef enum {
+    MDC_OK = 0,
+    MDC_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, bad flag */
+    MDC_ERR_SHAPE = 2,         /* e.g. reciprocity requested with nr != nv, nb > nb_max */
+    MDC_ERR_INDEX_RANGE = 3,   /* a source index outside [0, ns) was seen on the device */
+    MDC_ERR_OOM = 4,           /* device allocation failed in mdc_plan_create */
+    MDC_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
+    MDC_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+    MDC_ERR_UNSUPPORTED = 7    /* size outside the supported range (nt > 4096, nfft not a power of two) */
+} mdc_status;
+
+typedef enum { MDC_PREC_FP32 = 0 } mdc_precision;
+
+/* Create a plan for one MDD problem and precompute the spectrum of the down-going wavefield
+ * (Appendix A: the kernel is transformed once; the per-frequency matrices Dh_f are ns x nr).
+ *   out     : receives the plan handle (host pointer).
+ *   nt      : time samples per trace, 1 <= nt <= 4096.
+ *   nr, nv, ns : receivers, virtual sources, sources (>= 1).
+ *   nb_max  : largest batch size later passed to any call (1 <= nb_max; 0 means ns).
+ *   nfft    : FFT length; 0 picks the smallest power of two >= max(2*nt-1, 64).  A non-zero value
+ *             must be a power of two >= 2*nt-1 and <= 8192.
+ *   scale   : multiplies the operator (the discretisation of the receiver integral in Eq. 1; 1 is a
+ *             plain sum over receivers).
+ *   D       : device pointer, [ns][nr][nt] float32, read during this call only.
+ *   precision : MDC_PREC_FP32 (FFTs and complex products in float32).
+ *   stream  : stream for the precompute; the call returns after it has been enqueued.
+ * Allocates about 8*nf*(ns+nv)*nr + 8*nf*nv*nb_max bytes of device memory (nf = nfft/2+1). */
+int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max, int nfft,
+                    float scale, const float *D, int precision, void *stream);
+
+/* Release a plan and its device memory (synchronises the device first).  NULL is accepted. */
+int mdc_plan_destroy(mdc_plan_t plan);
+
+/* Sizes chosen by the plan: FFT length and number of frequency bins (nfft/2+1).  Host pointers,
+ * either may be NULL. */
+int mdc_plan_info(mdc_plan_t plan, int *nfft, int *nf);
+
+/* Largest squared singular value of the frequency-domain kernel, max over bins f of
+ * lambda_max(Dh_f^H Dh_f) * scale^2, by n_iter power iterations per bin (Appendix B: the singular
+ * values of the MDC operator are those of the kernel; alpha_max = 2 / sigma^2 for the Landweber
+ * iteration).  The result is a lower bound of the exact value that converges as n_iter grows.
+ * Blocks until the value is on the host.  sigma2 is a host pointer. */
+int mdc_plan_sigma2_max(mdc_plan_t plan, int n_iter, double *sigma2, void *stream);
+
+/* Forward MDC for a batch of sources (Eq. 1-3 in the time domain, one batch of Eq. 5).
+ *   X : [nv][nr][nt] device float32.  idx : device int32[nb], entries in [0, ns), duplicates allowed.
+ *   U : [nb][nv][nt] device float32, written.  1 <= nb <= nb_max. */
+int mdc_forward(mdc_plan_t plan, const float *X, const int32_t *idx, int nb, float *U, void *stream);
+
+/* Adjoint MDC (cross-correlation with the down-going field; the operator P+^H of Eq. 6).
+ *   R : [nb][nv][nt] device float32.  idx as for mdc_forward.  G : [nv][nr][nt] device float32, written. */
+int mdc_adjoint(mdc_plan_t plan, const float *R, const int32_t *idx, int nb, float *G, void *stream);
+
+/* smdd_params.flags */
+#define SMDD_RECIPROCITY    1   /* apply C_r: the step uses 1/2 (g + g^T) (needs nr == nv) */
+#define SMDD_KEEP_XHAT      2   /* after the update, leave the spectrum of the new X in the plan */
+#define SMDD_REUSE_XHAT     4   /* start from the spectrum left by the previous KEEP_XHAT step on the
+                                   same X pointer (the caller promises X was not modified in between;
+                                   ignored if the plan holds no spectrum for this pointer) */
+#define SMDD_UOBS_GATHERED  8   /* U_obs is [nb][nv][nt]: the batch rows, already gathered */
+
+typedef struct {
+    float alpha;        /* step size (Appendix B: a fraction of 2 / sigma^2) */
+    int flags;          /* SMDD_* bits */
+    int reserved[6];    /* must be zero */
+} smdd_params;
+
+/* One stochastic MDD step on the batch idx (Eq. 6 and the SGD update):
+ *   R = P_B X - U_obs[idx],  loss = 1/2 ||R||^2 (accumulated in float64),
+ *   g = P_B^H R,  X <- X - alpha * C(g),  C = C_r (reciprocity flag) or the identity.
+ *   X     : [nv][nr][nt] device float32, updated in place.
+ *   U_obs : [ns][nv][nt] (or [nb][nv][nt] with SMDD_UOBS_GATHERED) device float32.
+ *   idx   : device int32[nb].   params : host pointer.
+ *   loss  : device float64 scalar written with 1/2 ||R||^2, or NULL. */
+int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
+              const smdd_params *params, double *loss, void *stream);
+
+/* Wait for all work of this plan's device, then return and clear the device-side status word
+ * (MDC_OK or MDC_ERR_INDEX_RANGE). */
+int mdc_plan_sync_status(mdc_plan_t plan);
+
+/* Human-readable name of a status code (static string). */
+const char *mdc_status_string(int status);
+
+/* Stage timing and launch counting, for measurement.  When enabled, every kernel launch of the plan
+ * is bracketed by CUDA events recorded on the launch stream.  mdc_plan_stage_times() waits for those
+ * events and returns, per stage, the summed device milliseconds and the number of launches since the
+ * last reset (arrays of MDC_NUM_STAGES entries, host pointers; either may be NULL). */
+#define MDC_NUM_STAGES 7   /* rfft, cgemm_fwd, residual, cgemm_adj, update, irfft_out, setup */
+int mdc_plan_set_profiling(mdc_plan_t plan, int enable);
+int mdc_plan_stage_times(mdc_plan_t plan, double *ms, long long *launches, int reset);
+const char *mdc_stage_name(int stage);
+/* Total kernel launches made by this plan since creation (host counter). */
+long long mdc_plan_launch_count(mdc_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMDD_H */

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of libsmdd_gb300.so (the C ABI declared in include/smdd.h).
+
+Argument marshalling only: every function here checks the torch tensors it is given (device, dtype,
+contiguity, shape), passes their device pointers and the current CUDA stream to the C function of the
+same name, and raises MDCError on a non-zero status.  All arithmetic runs in the library's CUDA
+kernels; there is no CPU fallback.  If the library is missing or no CUDA device is present, the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmdd_gb300.so")
+
+MDC_OK = 0
+MDC_ERR_INVALID_ARG = 1
+MDC_ERR_SHAPE = 2
+MDC_ERR_INDEX_RANGE = 3
+MDC_ERR_OOM = 4
+MDC_ERR_CUDA = 5
+MDC_ERR_TIMEOUT = 6
+MDC_ERR_UNSUPPORTED = 7
+
+SMDD_RECIPROCITY = 1
+SMDD_KEEP_XHAT = 2
+SMDD_REUSE_XHAT = 4
+SMDD_UOBS_GATHERED = 8
+
+MDC_NUM_STAGES = 7
+
+EXPORTED = (
+    "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
+    "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
+    "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count",
+)
+
+
+class MDCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class smdd_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the in-tree library (no GPU needed to load it).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2202_04486_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    lib.mdc_plan_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, f, vp, i, vp]
+    lib.mdc_plan_destroy.argtypes = [vp]
+    lib.mdc_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.mdc_plan_sigma2_max.argtypes = [vp, i, ctypes.POINTER(d), vp]
+    lib.mdc_forward.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.mdc_adjoint.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.smdd_step.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(smdd_params), vp, vp]
+    lib.mdc_plan_sync_status.argtypes = [vp]
+    lib.mdc_status_string.argtypes = [i]
+    lib.mdc_status_string.restype = ctypes.c_char_p
+    lib.mdc_plan_set_profiling.argtypes = [vp, i]
+    lib.mdc_plan_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]
+    lib.mdc_stage_name.argtypes = [i]
+    lib.mdc_stage_name.restype = ctypes.c_char_p
+    lib.mdc_plan_launch_count.argtypes = [vp]
+    lib.mdc_plan_launch_count.restype = ctypes.c_longlong
+    for name in EXPORTED:
+        if name not in ("mdc_status_string", "mdc_stage_name", "mdc_plan_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().mdc_status_string(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != MDC_OK:
+        raise MDCError(rc, where)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype, shape=None) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the stochastic MDD kernels run only on the GPU")
+
+
+# ------------------------------------------------------------------------------------------------
+# functions with the C names (plan handles are plain integers)
+# ------------------------------------------------------------------------------------------------
+def mdc_plan_create(D: torch.Tensor, nv: int, nb_max: int = 0, nfft: int = 0, scale: float = 1.0,
+                    precision: int = 0, stream=None) -> int:
+    _require_cuda()
+    lib = load_library()
+    ns, nr, nt = D.shape
+    h = ctypes.c_void_p()
+    _check(lib.mdc_plan_create(ctypes.byref(h), nt, nr, nv, ns, nb_max, nfft, float(scale),
+                               _dev(D, "D", torch.float32), precision, _stream_ptr(stream)), "mdc_plan_create")
+    return h.value
+
+
+def mdc_plan_destroy(plan: int) -> None:
+    _check(load_library().mdc_plan_destroy(ctypes.c_void_p(plan)), "mdc_plan_destroy")
+
+
+def mdc_plan_info(plan: int) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().mdc_plan_info(ctypes.c_void_p(plan), ctypes.byref(a), ctypes.byref(b)), "mdc_plan_info")
+    return a.value, b.value
+
+
+def mdc_plan_sigma2_max(plan: int, n_iter: int = 60, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load_library().mdc_plan_sigma2_max(ctypes.c_void_p(plan), n_iter, ctypes.byref(out), _stream_ptr(stream)),
+           "mdc_plan_sigma2_max")
+    return out.value
+
+
+def mdc_forward(plan: int, X: torch.Tensor, idx: torch.Tensor, U: torch.Tensor, stream=None) -> torch.Tensor:
+    nb = idx.numel()
+    _check(load_library().mdc_forward(ctypes.c_void_p(plan), _dev(X, "X", torch.float32), _dev(idx, "idx", torch.int32),
+                                      nb, _dev(U, "U", torch.float32), _stream_ptr(stream)), "mdc_forward")
+    return U
+
+
+def mdc_adjoint(plan: int, R: torch.Tensor, idx: torch.Tensor, G: torch.Tensor, stream=None) -> torch.Tensor:
+    nb = idx.numel()
+    _check(load_library().mdc_adjoint(ctypes.c_void_p(plan), _dev(R, "R", torch.float32), _dev(idx, "idx", torch.int32),
+                                      nb, _dev(G, "G", torch.float32), _stream_ptr(stream)), "mdc_adjoint")
+    return G
+
+
+def smdd_step(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor, alpha: float, flags: int = 0,
+              loss: torch.Tensor | None = None, stream=None) -> None:
+    p = smdd_params(float(alpha), int(flags))
+    lp = ctypes.c_void_p(0) if loss is None else _dev(loss, "loss", torch.float64)
+    _check(load_library().smdd_step(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
+                                    _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
+                                    ctypes.byref(p), lp, _stream_ptr(stream)), "smdd_step")
+
+
+def mdc_plan_sync_status(plan: int) -> int:
+    return int(load_library().mdc_plan_sync_status(ctypes.c_void_p(plan)))
+
+
+def mdc_plan_set_profiling(plan: int, enable: bool) -> None:
+    _check(load_library().mdc_plan_set_profiling(ctypes.c_void_p(plan), int(bool(enable))), "mdc_plan_set_profiling")
+
+
+def mdc_plan_stage_times(plan: int, reset: bool = False) -> dict:
+    lib = load_library()
+    ms = (ctypes.c_double * MDC_NUM_STAGES)()
+    n = (ctypes.c_longlong * MDC_NUM_STAGES)()
+    _check(lib.mdc_plan_stage_times(ctypes.c_void_p(plan), ms, n, int(reset)), "mdc_plan_stage_times")
+    return {lib.mdc_stage_name(s).decode(): (ms[s], n[s]) for s in range(MDC_NUM_STAGES)}
+
+
+def mdc_plan_launch_count(plan: int) -> int:
+    return int(load_library().mdc_plan_launch_count(ctypes.c_void_p(plan)))
+
+
+# ------------------------------------------------------------------------------------------------
+# convenience object
+# ------------------------------------------------------------------------------------------------
+class MDCPlan:
+    """Owns one C plan: D is transformed once at construction; the methods wrap the C calls."""
+
+    def __init__(self, D: torch.Tensor, nv: int, nb_max: int = 0, nfft: int = 0, scale: float = 1.0, stream=None):
+        self.ns, self.nr, self.nt = D.shape
+        self.nv = nv
+        self.nb_max = nb_max or self.ns
+        self.handle = mdc_plan_create(D, nv, nb_max, nfft, scale, 0, stream)
+        self.nfft, self.nf = mdc_plan_info(self.handle)
+        self.device = D.device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mdc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sigma2_max(self, n_iter: int = 60) -> float:
+        return mdc_plan_sigma2_max(self.handle, n_iter)
+
+    def forward(self, X: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((idx.numel(), self.nv, self.nt), device=X.device, dtype=torch.float32)
+        return mdc_forward(self.handle, X, idx, out)
+
+    def adjoint(self, R: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.nv, self.nr, self.nt), device=R.device, dtype=torch.float32)
+        return mdc_adjoint(self.handle, R, idx, out)
+
+    def step(self, X, U_obs, idx, alpha, flags=0, loss=None):
+        smdd_step(self.handle, X, U_obs, idx, alpha, flags, loss)
+
+    def sync_status(self) -> int:
+        return mdc_plan_sync_status(self.handle)

@@ -1,0 +1,490 @@
+// C ABI of the stochastic MDD hot path: plan management, the operator entry points and the SGD step.
+// See include/smdd.h for the contract of every function.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "smdd_fft.cuh"
+#include "smdd_internal.h"
+
+using namespace smdd;
+
+namespace {
+
+struct PendingTiming {
+    int stage;
+    cudaEvent_t e0, e1;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+struct mdc_plan_s {
+    int device = 0;
+    int nt = 0, nr = 0, nv = 0, ns = 0, nbmax = 0, nfft = 0, M = 0, nf = 0;
+    int ldr = 0, ldb = 0;
+    float scale = 1.f;
+    float2 *Dh = nullptr;        // [nf][ns][ldr]
+    float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
+    float2 *Uh = nullptr;        // [nf][nv][ldb]  batch spectra (prediction, then residual)
+    float2 *twM = nullptr;       // [M]
+    float2 *twN = nullptr;       // [M+1]
+    double *partials = nullptr;  // residual-kernel block partials
+    double *lam = nullptr;       // [nf] power-iteration results, [nf] = max
+    unsigned int *counter = nullptr;
+    int *status = nullptr;
+    int resid_blocks_max = 0;
+    const float *xhat_for = nullptr;  // model pointer whose spectrum Xh holds (KEEP_XHAT)
+    bool profiling = false;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[MDC_NUM_STAGES] = {0};
+    long long stage_launches[MDC_NUM_STAGES] = {0};
+    long long launches = 0;
+};
+
+namespace {
+
+cudaEvent_t get_event(mdc_plan_s *p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <class F>
+int launch_stage(mdc_plan_s *p, int stage, cudaStream_t st, F &&fn) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->profiling) {
+        e0 = get_event(p);
+        e1 = get_event(p);
+        cudaEventRecord(e0, st);
+    }
+    const cudaError_t err = fn();
+    if (p->profiling) {
+        cudaEventRecord(e1, st);
+        p->pending.push_back({stage, e0, e1});
+    }
+    p->launches++;
+    p->stage_launches[stage]++;
+    if (err != cudaSuccess) {
+        fprintf(stderr, "smdd: launch of stage %d failed: %s\n", stage, cudaGetErrorString(err));
+        return MDC_ERR_CUDA;
+    }
+    return MDC_OK;
+}
+
+FftArgs base_fft(const mdc_plan_s *p) {
+    FftArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nt = p->nt;
+    a.twM = p->twM;
+    a.twN = p->twN;
+    a.s = p->scale / (float)p->nfft;
+    a.status = p->status;
+    return a;
+}
+
+int ti_log2_for(int n_contig, int TR) {
+    // as many consecutive traces along the contiguous spectrum axis as the tile holds
+    int l = 0;
+    while ((1 << (l + 1)) <= TR && (1 << l) < n_contig) ++l;
+    return l;
+}
+
+int traces_per_cta(int M) { return M <= 512 ? 16 : 8192 / M; }
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+// model-layout grid: trace (i = r, j = v) of a [nv][nr][nt] array  <->  spectra [nf][nv][ldr]
+TraceGrid model_grid(const mdc_plan_s *p, int nouter) {
+    TraceGrid g;
+    g.ni = p->nr;
+    g.nj = nouter;
+    g.ti_log2 = ti_log2_for(p->nr, traces_per_cta(p->M));
+    g.tsi = p->nt;
+    g.tsj = (long long)p->nr * p->nt;
+    g.ssi = 1;
+    g.ssj = p->ldr;
+    g.ssf = (long long)nouter * p->ldr;
+    return g;
+}
+
+// batch-layout grid: trace (i = b, j = v) of a [nb][nv][nt] array  <->  spectra [nf][nv][ldb]
+TraceGrid batch_grid(const mdc_plan_s *p, int nb) {
+    TraceGrid g;
+    g.ni = nb;
+    g.nj = p->nv;
+    g.ti_log2 = ti_log2_for(nb, traces_per_cta(p->M));
+    g.tsi = (long long)p->nv * p->nt;
+    g.tsj = p->nt;
+    g.ssi = 1;
+    g.ssj = p->ldb;
+    g.ssf = (long long)p->nv * p->ldb;
+    return g;
+}
+
+int rfft_model(mdc_plan_s *p, const float *X, cudaStream_t st) {
+    FftArgs a = base_fft(p);
+    a.g = model_grid(p, p->nv);
+    a.tin = X;
+    a.vec = (p->nt % 2 == 0) && aligned8(X);
+    a.spec = p->Xh;
+    return launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); });
+}
+
+int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.A = p->Xh;
+    g.Dh = p->Dh;
+    g.idx = idx;
+    g.C = p->Uh;
+    g.nv = p->nv; g.nr = p->nr; g.ns = p->ns; g.nb = nb; g.ldr = p->ldr; g.ldb = p->ldb;
+    g.sAf = (long long)p->nv * p->ldr;
+    g.sDf = (long long)p->ns * p->ldr;
+    g.sCf = (long long)p->nv * p->ldb;
+    g.outscale = 1.f;
+    g.status = p->status;
+    return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
+}
+
+int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStream_t st) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.A = p->Uh;
+    g.Dh = p->Dh;
+    g.idx = idx;
+    g.C = p->Xh;
+    g.nv = p->nv; g.nr = p->nr; g.ns = p->ns; g.nb = nb; g.ldr = p->ldr; g.ldb = p->ldb;
+    g.sAf = (long long)p->nv * p->ldb;
+    g.sDf = (long long)p->ns * p->ldr;
+    g.sCf = (long long)p->nv * p->ldr;
+    g.outscale = recip ? 0.5f : 1.f;
+    g.status = p->status;
+    return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st); });
+}
+
+int check_common(mdc_plan_s *p, const void *a, const void *b, const int32_t *idx, int nb) {
+    if (!p || !a || !b || !idx) return MDC_ERR_INVALID_ARG;
+    if (nb < 1) return MDC_ERR_INVALID_ARG;
+    if (nb > p->nbmax) return MDC_ERR_SHAPE;
+    return MDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mdc_status_string(int s) {
+    switch (s) {
+        case MDC_OK: return "MDC_OK";
+        case MDC_ERR_INVALID_ARG: return "MDC_ERR_INVALID_ARG";
+        case MDC_ERR_SHAPE: return "MDC_ERR_SHAPE";
+        case MDC_ERR_INDEX_RANGE: return "MDC_ERR_INDEX_RANGE";
+        case MDC_ERR_OOM: return "MDC_ERR_OOM";
+        case MDC_ERR_CUDA: return "MDC_ERR_CUDA";
+        case MDC_ERR_TIMEOUT: return "MDC_ERR_TIMEOUT";
+        case MDC_ERR_UNSUPPORTED: return "MDC_ERR_UNSUPPORTED";
+    }
+    return "MDC_ERR_UNKNOWN";
+}
+
+const char *mdc_stage_name(int stage) {
+    static const char *names[MDC_NUM_STAGES] = {"rfft", "cgemm_fwd", "residual", "cgemm_adj",
+                                                "update", "irfft_out", "setup"};
+    return (stage >= 0 && stage < MDC_NUM_STAGES) ? names[stage] : "unknown";
+}
+
+int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max, int nfft, float scale,
+                    const float *D, int precision, void *stream) {
+    if (!out || !D) return MDC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nt < 1 || nr < 1 || nv < 1 || ns < 1 || nb_max < 0) return MDC_ERR_INVALID_ARG;
+    if (precision != MDC_PREC_FP32) return MDC_ERR_UNSUPPORTED;
+    if (!std::isfinite(scale)) return MDC_ERR_INVALID_ARG;
+    if (nt > 4096) return MDC_ERR_UNSUPPORTED;
+    if (nfft == 0) {
+        nfft = 64;
+        while (nfft < 2 * nt - 1) nfft *= 2;
+    } else if (!is_pow2(nfft) || nfft < 2 * nt - 1 || nfft < 64 || nfft > 8192) {
+        return MDC_ERR_UNSUPPORTED;
+    }
+    if (nb_max == 0) nb_max = ns;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    mdc_plan_s *p = new (std::nothrow) mdc_plan_s();
+    if (!p) return MDC_ERR_OOM;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return MDC_ERR_CUDA; }
+    p->nt = nt; p->nr = nr; p->nv = nv; p->ns = ns; p->nbmax = nb_max;
+    p->nfft = nfft; p->M = nfft / 2; p->nf = nfft / 2 + 1;
+    p->ldr = (nr + 1) & ~1;
+    p->ldb = (nb_max + 1) & ~1;
+    p->scale = scale;
+
+    const int M = p->M, nf = p->nf;
+    const size_t szD = (size_t)nf * ns * p->ldr * sizeof(float2);
+    const size_t szX = (size_t)nf * nv * p->ldr * sizeof(float2);
+    const size_t szU = (size_t)nf * nv * p->ldb * sizeof(float2);
+    {
+        TraceGrid g = batch_grid(p, nb_max);
+        p->resid_blocks_max = fft_blocks(M, g);
+    }
+    bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
+              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->twM, M * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->twN, (M + 1) * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->partials, (size_t)(p->resid_blocks_max + 1) * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&p->lam, (size_t)(nf + 1) * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&p->counter, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&p->status, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        mdc_plan_destroy(p);
+        return MDC_ERR_OOM;
+    }
+    // twiddles in double precision, rounded once to float
+    std::vector<float2> tw(M + 1);
+    const double pi = 3.14159265358979323846;
+    for (int m = 0; m < M; ++m) {
+        const double ang = 2.0 * pi * (double)m / (double)M;
+        tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    int rc = MDC_OK;
+    if (cudaMemcpyAsync(p->twM, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    std::vector<float2> twn(M + 1);
+    for (int k = 0; k <= M; ++k) {
+        const double ang = 2.0 * pi * (double)k / (double)nfft;
+        twn[k] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    if (cudaMemcpyAsync(p->twN, twn.data(), (M + 1) * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemsetAsync(p->counter, 0, sizeof(unsigned int), st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemsetAsync(p->Dh, 0, szD, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemsetAsync(p->Xh, 0, szX, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemsetAsync(p->Uh, 0, szU, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (rc == MDC_OK && (fft_prepare(M) != cudaSuccess || gemm_prepare() != cudaSuccess)) rc = MDC_ERR_CUDA;
+    if (rc == MDC_OK) {
+        // kernel spectra: D [ns][nr][nt] -> Dh [nf][ns][ldr] (same layout rule as the model)
+        FftArgs a = base_fft(p);
+        a.g = model_grid(p, ns);
+        a.tin = D;
+        a.vec = (nt % 2 == 0) && aligned8(D);
+        a.spec = p->Dh;
+        rc = launch_stage(p, ST_SETUP, st, [&] { return launch_rfft(M, a, st); });
+    }
+    if (rc == MDC_OK) {
+        // the host twiddle vectors must outlive the asynchronous copies
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    }
+    if (rc != MDC_OK) {
+        mdc_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return MDC_OK;
+}
+
+int mdc_plan_destroy(mdc_plan_t p) {
+    if (!p) return MDC_OK;
+    DeviceGuard dg(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->Dh);
+    cudaFree(p->Xh);
+    cudaFree(p->Uh);
+    cudaFree(p->twM);
+    cudaFree(p->twN);
+    cudaFree(p->partials);
+    cudaFree(p->lam);
+    cudaFree(p->counter);
+    cudaFree(p->status);
+    for (auto &t : p->pending) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
+    delete p;
+    return MDC_OK;
+}
+
+int mdc_plan_info(mdc_plan_t p, int *nfft, int *nf) {
+    if (!p) return MDC_ERR_INVALID_ARG;
+    if (nfft) *nfft = p->nfft;
+    if (nf) *nf = p->nf;
+    return MDC_OK;
+}
+
+int mdc_plan_sigma2_max(mdc_plan_t p, int n_iter, double *sigma2, void *stream) {
+    if (!p || !sigma2 || n_iter < 1) return MDC_ERR_INVALID_ARG;
+    if ((size_t)(2 * p->nr + p->ns) * 16 > 227 * 1024) return MDC_ERR_UNSUPPORTED;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_stage(p, ST_SETUP, st, [&] {
+        return launch_power_iter(p->Dh, p->ns, p->nr, p->ldr, (long long)p->ns * p->ldr, p->nf, n_iter, p->lam, st);
+    });
+    if (rc) return rc;
+    rc = launch_stage(p, ST_SETUP, st, [&] { return launch_max_reduce(p->lam, p->nf, p->lam + p->nf, st); });
+    if (rc) return rc;
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, p->lam + p->nf, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MDC_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MDC_ERR_CUDA;
+    *sigma2 = v * (double)p->scale * (double)p->scale;
+    return MDC_OK;
+}
+
+int mdc_forward(mdc_plan_t p, const float *X, const int32_t *idx, int nb, float *U, void *stream) {
+    int rc = check_common(p, X, U, idx, nb);
+    if (rc) return rc;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    p->xhat_for = nullptr;
+    if ((rc = rfft_model(p, X, st))) return rc;
+    if ((rc = gemm_forward(p, idx, nb, st))) return rc;
+    FftArgs a = base_fft(p);
+    a.g = batch_grid(p, nb);
+    a.tout = U;
+    a.vec = (p->nt % 2 == 0) && aligned8(U);
+    a.spec = p->Uh;
+    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
+}
+
+int mdc_adjoint(mdc_plan_t p, const float *R, const int32_t *idx, int nb, float *G, void *stream) {
+    int rc = check_common(p, R, G, idx, nb);
+    if (rc) return rc;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    p->xhat_for = nullptr;
+    {
+        FftArgs a = base_fft(p);
+        a.g = batch_grid(p, nb);
+        a.tin = R;
+        a.vec = (p->nt % 2 == 0) && aligned8(R);
+        a.spec = p->Uh;
+        if ((rc = launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); }))) return rc;
+    }
+    if ((rc = gemm_adjoint(p, idx, nb, false, st))) return rc;
+    FftArgs a = base_fft(p);
+    a.g = model_grid(p, p->nv);
+    a.tout = G;
+    a.vec = (p->nt % 2 == 0) && aligned8(G);
+    a.spec = p->Xh;
+    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
+}
+
+int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb, const smdd_params *prm,
+              double *loss, void *stream) {
+    int rc = check_common(p, X, U_obs, idx, nb);
+    if (rc) return rc;
+    if (!prm) return MDC_ERR_INVALID_ARG;
+    const int flags = prm->flags;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
+    const bool recip = flags & SMDD_RECIPROCITY;
+    if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // a1: model spectra (or the ones left by the previous step's fused update)
+    if (!((flags & SMDD_REUSE_XHAT) && p->xhat_for == X)) {
+        if ((rc = rfft_model(p, X, st))) return rc;
+    }
+    p->xhat_for = nullptr;
+    // a2 + a3: gathered kernel rows x model spectra
+    if ((rc = gemm_forward(p, idx, nb, st))) return rc;
+    // a4 + a5: inverse FFT, window, residual, loss, residual spectra
+    {
+        FftArgs a = base_fft(p);
+        a.g = batch_grid(p, nb);
+        a.spec = p->Uh;
+        a.uobs = U_obs;
+        a.idx = idx;
+        a.ns = p->ns;
+        a.gathered = (flags & SMDD_UOBS_GATHERED) ? 1 : 0;
+        a.uo_si = (long long)p->nv * p->nt;
+        a.uo_sj = p->nt;
+        a.vec = (p->nt % 2 == 0) && aligned8(U_obs);
+        a.partials = p->partials;
+        a.counter = p->counter;
+        a.loss = loss;
+        if ((rc = launch_stage(p, ST_RESID, st, [&] { return launch_residual(p->M, a, p->resid_blocks_max, st); })))
+            return rc;
+    }
+    // a6: gradient spectra (with the reciprocity projection folded in)
+    if ((rc = gemm_adjoint(p, idx, nb, recip, st))) return rc;
+    // a7 + a8: inverse FFT, window, update, and optionally the spectra of the new model
+    {
+        const bool keep = flags & SMDD_KEEP_XHAT;
+        FftArgs a = base_fft(p);
+        a.g = model_grid(p, p->nv);
+        a.tout = X;
+        a.vec = (p->nt % 2 == 0) && aligned8(X);
+        a.spec = p->Xh;
+        a.alpha = prm->alpha;
+        if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;
+        if (keep) p->xhat_for = X;
+    }
+    return MDC_OK;
+}
+
+int mdc_plan_sync_status(mdc_plan_t p) {
+    if (!p) return MDC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return MDC_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MDC_ERR_CUDA;
+    if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return MDC_ERR_CUDA;
+    return h ? MDC_ERR_INDEX_RANGE : MDC_OK;
+}
+
+int mdc_plan_set_profiling(mdc_plan_t p, int enable) {
+    if (!p) return MDC_ERR_INVALID_ARG;
+    p->profiling = enable != 0;
+    return MDC_OK;
+}
+
+int mdc_plan_stage_times(mdc_plan_t p, double *ms, long long *launches, int reset) {
+    if (!p) return MDC_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    for (auto &t : p->pending) {
+        if (cudaEventSynchronize(t.e1) != cudaSuccess) return MDC_ERR_CUDA;
+        float el = 0.f;
+        if (cudaEventElapsedTime(&el, t.e0, t.e1) != cudaSuccess) return MDC_ERR_CUDA;
+        p->stage_ms[t.stage] += el;
+        p->event_pool.push_back(t.e0);
+        p->event_pool.push_back(t.e1);
+    }
+    p->pending.clear();
+    for (int s = 0; s < MDC_NUM_STAGES; ++s) {
+        if (ms) ms[s] = p->stage_ms[s];
+        if (launches) launches[s] = p->stage_launches[s];
+        if (reset) {
+            p->stage_ms[s] = 0.0;
+            p->stage_launches[s] = 0;
+        }
+    }
+    return MDC_OK;
+}
+
+long long mdc_plan_launch_count(mdc_plan_t p) { return p ? p->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of libsmdd_gb300.so (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/smdd.h"
+
+namespace smdd {
+
+enum Stage { ST_RFFT = 0, ST_GEMM_FWD = 1, ST_RESID = 2, ST_GEMM_ADJ = 3, ST_UPDATE = 4, ST_IRFFT_OUT = 5, ST_SETUP = 6 };
+
+// A 2-D grid of time traces and the matching spectra.  Trace (i, j), i < ni, j < nj:
+//   time samples at  tin/tout + i*tsi + j*tsj + t          (floats),  t < nt
+//   spectrum bin f at spec + f*ssf + i*ssi + j*ssj           (float2), f <= M
+// A CTA owns TR traces: 2^ti_log2 consecutive i times TR >> ti_log2 consecutive j.
+struct TraceGrid {
+    int ni, nj, ti_log2;
+    long long tsi, tsj;
+    long long ssi, ssj, ssf;
+};
+
+struct FftArgs {
+    TraceGrid g;
+    int nt;
+    int vec;                 // time traces may be accessed as float2 (nt even, 8-byte aligned)
+    const float *tin;        // time input (rfft)
+    float *tout;             // time output (irfft_out) / model in-out (update)
+    float2 *spec;            // spectra (read and/or written)
+    const float2 *twM;       // exp(-2 pi i m / M), m < M
+    const float2 *twN;       // exp(-2 pi i k / N), k <= M
+    float s;                 // epilogue factor scale / N
+    float alpha;             // step size (update)
+    // residual: observed rows, row(i) = gathered ? i : idx[i]
+    const float *uobs;
+    const int32_t *idx;
+    int ns, gathered;
+    long long uo_si, uo_sj;
+    double *partials;
+    unsigned int *counter;
+    double *loss;
+    int *status;
+};
+
+struct GemmArgs {
+    const float2 *A;         // forward: model spectra Xh; adjoint: residual spectra Rh
+    const float2 *Dh;        // kernel spectra [nf][ns][ldr]
+    const int32_t *idx;
+    float2 *C;               // forward: Uh; adjoint: Gh
+    int nv, nr, ns, nb, ldr, ldb;
+    long long sAf, sDf, sCf; // per-frequency strides (float2)
+    float outscale;
+    int tiles_v, tiles_r;    // adjoint tile grid
+    int *status;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st);
+cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st);
+cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st);
+cudaError_t launch_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
+int fft_blocks(int M, const TraceGrid &g);
+cudaError_t fft_prepare(int M);   // opt-in to the dynamic shared memory the kernels of size M need
+
+cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
+cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
+cudaError_t gemm_prepare();
+
+cudaError_t launch_power_iter(const float2 *Dh, int ns, int nr, int ldr, long long sDf, int nf, int n_iter,
+                              double *lam, cudaStream_t st);
+cudaError_t launch_max_reduce(const double *lam, int n, double *out, cudaStream_t st);
+
+}  // namespace smdd

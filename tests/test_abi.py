@@ -1,0 +1,62 @@
+"""C-ABI checks that need no GPU: the library builds, loads, and exports every function that
+include/*.h declares; the binding refuses to run without a CUDA device (no CPU fallback)."""
+import glob
+import os
+import re
+
+import pytest
+import torch
+
+from paper_2202_04486_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:(?:unsigned|long|signed)\s+)*[A-Za-z_]\w*(?:\s+|\s*\*+\s*)([a-z_]\w*)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("mdc_plan_create", "mdc_forward", "mdc_adjoint", "smdd_step", "mdc_plan_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(binding.EXPORTED) <= set(_declared_functions())
+
+
+def test_status_strings(lib):
+    assert binding.status_string(0) == "MDC_OK"
+    assert binding.status_string(3) == "MDC_ERR_INDEX_RANGE"
+    assert binding.status_string(99) == "MDC_ERR_UNKNOWN"
+
+
+def test_null_arguments_rejected_without_touching_the_gpu(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    # null output pointer / null D: host-side validation, nothing launched
+    assert lib.mdc_plan_create(None, 8, 2, 2, 2, 0, 0, 1.0, None, 0, None) == binding.MDC_ERR_INVALID_ARG
+    assert lib.mdc_plan_create(ctypes.byref(h), 8, 2, 2, 2, 0, 0, 1.0, None, 0, None) == binding.MDC_ERR_INVALID_ARG
+    assert lib.mdc_forward(None, None, None, 1, None, None) == binding.MDC_ERR_INVALID_ARG
+    assert lib.mdc_plan_destroy(None) == binding.MDC_OK
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_binding_fails_loudly_without_cuda():
+    with pytest.raises(RuntimeError):
+        binding.mdc_plan_create(torch.zeros(2, 2, 8), 2)
