@@ -1,0 +1,519 @@
+"""Benchmark of the stochastic MDD hot path: one SGD step (forward MDC on a source batch, residual,
+adjoint, reciprocity-preconditioned update) per timed iteration, on synthetic data shaped like the
+paper's workloads.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).  `value` is the algorithmic FLOP rate of the whole job:
+F_step = 16 nb nr nv nf (forward + adjoint complex products, 8 real flops per complex MAC)
+       + 5 nfft log2(nfft) (nr nv + nb nv) (two real FFTs per model trace and per residual trace,
+         2.5 N log2 N flops each), summed over the steps of all ranks, divided by the max over ranks of
+the device time of the K timed steps.  L2 is flushed (256 MiB write) before every timed step and the
+flush is outside the per-step CUDA events.
+
+--impl reference times the FP64 oracle (direct time-domain sums, OpenMP on the host cores) on a bounded
+sample of each step (a subset of virtual-source columns; forward and adjoint cost are linear in the
+number of columns) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2202_04486_gb300 import synth  # noqa: E402
+
+DEFAULT_WORKLOAD = "smdd_nt512_n201_nb16_recip"
+METRIC = "MDC fwd+adj GFLOP/s (SMDD step)"
+UNIT = "GFLOP/s"
+
+
+# ------------------------------------------------------------------------------------------------
+# work model
+# ------------------------------------------------------------------------------------------------
+def nfft_for(nt: int) -> int:
+    n = 64
+    while n < 2 * nt - 1:
+        n *= 2
+    return n
+
+
+def step_flops(nt, nr, nv, nb) -> float:
+    nfft = nfft_for(nt)
+    nf = nfft // 2 + 1
+    return 16.0 * nb * nr * nv * nf + 5.0 * nfft * math.log2(nfft) * (nr * nv + nb * nv)
+
+
+def step_bytes_compulsory(nt, nr, nv, nb, recip) -> float:
+    nfft = nfft_for(nt)
+    nf = nfft // 2 + 1
+    b = 2 * nr * nv * nt * 4 + nf * nb * nr * 8 + nb * nv * nt * 4
+    if recip:
+        b += 2 * nr * nv * nt * 4
+    return float(b)
+
+
+def kernel_work(stage, nt, nr, nv, nb):
+    """Algorithmic bytes and flops of one launch of a stage (see the design notes for the derivation)."""
+    nfft = nfft_for(nt)
+    nf = nfft // 2 + 1
+    fft_flops = 2.5 * nfft * math.log2(nfft)
+    if stage == "update":      # read Gh, read X, write X, write Xh (fused re-transform)
+        return dict(bytes=nv * nr * (2 * nf * 8 + 2 * nt * 4), flops=2 * fft_flops * nv * nr)
+    if stage == "cgemm_fwd":   # read Xh, gathered kernel rows, write Uh
+        return dict(bytes=nf * (nv * nr + nb * nr + nv * nb) * 8, flops=8.0 * nv * nr * nb * nf)
+    if stage == "cgemm_adj":   # read Rh, gathered kernel rows, write Gh
+        return dict(bytes=nf * (nv * nb + nb * nr + nv * nr) * 8, flops=8.0 * nv * nr * nb * nf)
+    if stage == "residual":    # read Uh, read U_obs rows, write Rh
+        return dict(bytes=nb * nv * (2 * nf * 8 + nt * 4), flops=2 * fft_flops * nb * nv)
+    if stage == "rfft":        # read X, write Xh
+        return dict(bytes=nv * nr * (nt * 4 + nf * 8), flops=fft_flops * nv * nr)
+    return dict(bytes=0, flops=0)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 SIMT peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2202_04486_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage: str, workload: str):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, or None when the summary is
+    missing or was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash, table = None, {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line.startswith("source_hash:"):
+                src_hash = line.split(":", 1)[1].strip()
+            elif line and not line.startswith("#") and ":" not in line:
+                parts = line.split()
+                if len(parts) >= 2:
+                    try:
+                        table[parts[0]] = float(parts[1])
+                    except ValueError:
+                        pass
+    if src_hash != kernel_source_hash():
+        return None
+    return table.get(stage)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.seek(0)
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smmax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smmax) if smmax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# problem set-up (both arms)
+# ------------------------------------------------------------------------------------------------
+def make_inputs(w, seed):
+    n = w.get("n") or 0
+    nt, nb = w["nt"], w["nb"]
+    nr, nv, ns = w.get("nr", n), w.get("nv", n), w.get("ns", n)
+    p = synth.make_problem(nt, nr, nv, ns, dx=w["dx"], n_reflectors=w["n_reflectors"],
+                           n_multiples=w["n_multiples"], seed=seed)
+    return p
+
+
+def workload_dims(name):
+    w = dict(synth.WORKLOADS[name])
+    nums = {"smdd_nt128_n32_nb8": (32, 32, 32), "smdd_nt512_n201_nb16_recip": (201, 201, 201),
+            "smdd_nt512_n256_nb16_recip": (256, 256, 256), "smdd_nt1024_n301_ns401_nb32": (301, 301, 401)}
+    w["nr"], w["nv"], w["ns"] = nums[name]
+    return w
+
+
+# ------------------------------------------------------------------------------------------------
+# oracle (CPU) timing: used for cpu_baseline and for --impl reference
+# ------------------------------------------------------------------------------------------------
+def oracle_step_sample(D, X, U_obs, idx, vsel):
+    import oracle
+    U = oracle.mdc_forward(D, X, idx, vsel=vsel)
+    R = U - U_obs[idx][:, vsel]
+    G = oracle.mdc_adjoint(D, R, idx, vsel=np.arange(len(vsel)))
+    return G
+
+
+def time_oracle(w, D, X, U_obs, batches, target_s=12.0, max_cols=None):
+    """Time the oracle's forward+adjoint on a sample of virtual-source columns and extrapolate to a
+    full step.  Returns (GFLOP/s equivalent, seconds per full step, sample description, threads)."""
+    import oracle
+    nv = w["nv"]
+    idx = batches[0][0]
+    cols = 2
+    t0 = time.perf_counter()
+    oracle_step_sample(D, X, U_obs, idx, np.arange(cols))
+    t1 = time.perf_counter()
+    per_col = max((t1 - t0) / cols, 1e-6)
+    k = int(min(nv if max_cols is None else max_cols, max(1, target_s / per_col)))
+    vsel = np.linspace(0, nv - 1, k).round().astype(np.int64)
+    t0 = time.perf_counter()
+    oracle_step_sample(D, X, U_obs, idx, vsel)
+    t1 = time.perf_counter()
+    t_step = (t1 - t0) * nv / k
+    f = step_flops(w["nt"], w["nr"], w["nv"], len(idx))
+    sample = (f"forward+adjoint direct sums (FP64) for {k} of {nv} virtual-source columns of one batch of "
+              f"{len(idx)} sources, extrapolated linearly in the column count ({t1 - t0:.1f} s measured)")
+    return f / t_step / 1e9, t_step, sample, oracle.num_threads()
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def run_gpu(args, rank, world, w):
+    import torch
+
+    from paper_2202_04486_gb300 import binding, build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(binding.LIB_PATH):
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    binding.load_library()
+    nt, nr, nv, ns, nb = w["nt"], w["nr"], w["nv"], w["ns"], w["nb"]
+    recip = bool(w["reciprocity"])
+
+    p = make_inputs(w, seed=rank)
+    D = torch.from_numpy(p.D.astype(np.float32)).to(dev)
+    X_true = torch.from_numpy(p.X_true.astype(np.float32)).to(dev)
+    # observed data: forward of the true model over all sources (GPU path) plus seeded noise
+    gen = binding.MDCPlan(D, nv, nb_max=ns)
+    U_obs = gen.forward(X_true, torch.arange(ns, dtype=torch.int32, device=dev))
+    if w["noise"] > 0:
+        rms = U_obs.pow(2).mean().sqrt()
+        U_obs += w["noise"] * rms * torch.from_numpy(p.noise.astype(np.float32)).to(dev)
+    gen.close()
+    del X_true
+
+    plan = binding.MDCPlan(D, nv, nb_max=nb)
+    sigma2 = plan.sigma2_max(60)
+    alpha = 0.5 * 2.0 / sigma2
+    flags = (binding.SMDD_RECIPROCITY if recip else 0) | binding.SMDD_KEEP_XHAT
+    X = torch.zeros((nv, nr, nt), device=dev)
+    n_ep = (args.warmup + args.steps) // math.ceil(ns / nb) + 2
+    batches = [b for ep in synth.epoch_batches(ns, nb, n_ep, seed=rank) for b in ep]
+    idx_dev = [torch.from_numpy(b).to(dev) for b in batches]
+    loss = torch.zeros(len(batches), device=dev, dtype=torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def one_step(k):
+        fl = flags | (binding.SMDD_REUSE_XHAT if k > 0 else 0)
+        binding.smdd_step(plan.handle, X, U_obs, idx_dev[k], alpha, fl, loss[k])
+
+    for k in range(args.warmup):
+        flush.fill_(float(k))
+        one_step(k)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each, per-step CUDA events on the launching stream
+    binding.mdc_plan_set_profiling(plan.handle, True)
+    binding.mdc_plan_stage_times(plan.handle, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = binding.mdc_plan_launch_count(plan.handle)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        smi_id = str(local)
+    with ClockSampler(smi_id) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            k = args.warmup + i
+            flush.fill_(float(k))
+            ev[i][0].record(stream)
+            one_step(k)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    launches = binding.mdc_plan_launch_count(plan.handle) - l0
+    stage = binding.mdc_plan_stage_times(plan.handle, reset=True)
+    binding.mdc_plan_set_profiling(plan.handle, False)
+    status = plan.sync_status()
+    if status != binding.MDC_OK:
+        raise RuntimeError(f"device status {binding.status_string(status)}")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    flops = sum(step_flops(nt, nr, nv, len(batches[args.warmup + i])) for i in range(args.steps))
+    losses = loss[: args.warmup + args.steps].cpu().numpy()
+
+    # e2e: the same steps with host inputs (pinned): batch index list and the batch rows of U_obs go
+    # host -> device every step, the loss comes back device -> host every step
+    U_host = U_obs.cpu().pin_memory()
+    Xe = torch.zeros_like(X)
+    Ub = torch.empty((nb, nv, nt), device=dev)
+    idx_host = [torch.from_numpy(b).pin_memory() for b in batches]
+    idx_buf = torch.empty(nb, dtype=torch.int32, device=dev)
+    loss_dev = torch.zeros((), device=dev, dtype=torch.float64)
+    loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
+    h2d = d2h = 0
+
+    def e2e_step(k, count):
+        nonlocal h2d, d2h
+        ih = idx_host[k]
+        n = ih.numel()
+        ib = idx_buf[:n]
+        ib.copy_(ih, non_blocking=True)
+        for b in range(n):
+            Ub[b].copy_(U_host[int(ih[b])], non_blocking=True)
+        fl = flags | binding.SMDD_UOBS_GATHERED | (binding.SMDD_REUSE_XHAT if k > 0 else 0)
+        binding.smdd_step(plan.handle, Xe, Ub[:n], ib, alpha, fl, loss_dev)
+        loss_host.copy_(loss_dev, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        _ = float(loss_host)
+        if count:
+            h2d += ih.numel() * 4 + n * nv * nt * 4
+            d2h += 8
+
+    for k in range(args.warmup):
+        e2e_step(k, False)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for i in range(args.steps):
+        e2e_step(args.warmup + i, True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - e0
+
+    # max over ranks
+    tt = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device=dev)
+    ff = torch.tensor([flops], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(ff, op=torch.distributed.ReduceOp.SUM)
+    t_dev, t_e2e, wall = tt.tolist()
+    flops_all = ff.item()
+    if rank != 0:
+        return None
+
+    peaks, peak_src = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    # dominant kernel: largest share of the device time of the timed steps
+    st = {k: v for k, v in stage.items() if v[1] > 0 and k in ("rfft", "cgemm_fwd", "residual", "cgemm_adj", "update")}
+    dom = max(st, key=lambda k: st[k][0])
+    dom_ms = st[dom][0] / st[dom][1]
+    kw = kernel_work(dom, nt, nr, nv, nb)
+    if dom in ("cgemm_fwd", "cgemm_adj"):
+        peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dom, args.workload),
+                "kernel": dom, "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                             f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        ach = kw["bytes"] / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dom, args.workload),
+                "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof["algorithmic_per_launch"] = kw["bytes"] if roof["bound"] == "hbm" else kw["flops"]
+    roof["launch_ms"] = round(dom_ms, 5)
+    stage_share = {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": v[1],
+                       "share": round(v[0] / sum(x[0] for x in st.values()), 4)} for k, v in st.items()}
+
+    # step-level roofline: max(compulsory bytes / HBM, flops / FP32 ALU peak)
+    fp32_peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    t_roof = max(step_bytes_compulsory(nt, nr, nv, nb, recip) / (peaks["hbm_gbs"] * 1e9),
+                 step_flops(nt, nr, nv, nb) / (fp32_peak * 1e12))
+    ms_per_step = t_dev / args.steps * 1e3
+
+    out = {
+        "metric": METRIC, "value": round(flops_all / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Ricker/hyperbola generator; U_obs = GPU forward of the true model + 5% noise)",
+        "config": {"workload": args.workload, "nt": nt, "nr": nr, "nv": nv, "ns": ns, "nb": nb,
+                   "nfft": nfft_for(nt), "reciprocity": recip, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
+                   "l2": "flushed before every timed step (256 MiB write, outside the step events)",
+                   "per_rank": "independent problem replica, seed = rank (no data-path collective)"},
+        "e2e": {"value": round(flops_all / t_e2e / 1e9, 2), "unit": UNIT,
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": int(launches) * world,
+        "roofline": roof,
+        "stage_share": stage_share,
+        "step_roofline": {"t_roof_us": round(t_roof * 1e6, 2), "t_step_us": round(ms_per_step * 1e3, 2),
+                          "frac": round(t_roof / (ms_per_step * 1e-3), 4),
+                          "definition": "max(compulsory bytes / measured HBM GB/s, algorithmic flops / FP32 SIMT peak)"},
+        "clocks": clocks,
+        "steps_per_s": round(args.steps / t_dev, 2),
+        "wall_s_timed_region": round(wall, 4),
+        "loss_first_last": [float(losses[0]), float(losses[-1])],
+    }
+    if world == 1 or rank == 0:
+        D64 = p.D.astype(np.float32).astype(np.float64)
+        Xs = np.zeros((nv, nr, nt))
+        Uo = U_obs.double().cpu().numpy()
+        val, t_step, sample, cores = time_oracle(w, D64, Xs, Uo, [batches[args.warmup:]])
+        out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample, "s_per_step_extrapolated": round(t_step, 3)}
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ------------------------------------------------------------------------------------------------
+def run_reference(args, rank, world, w):
+    if rank != 0:
+        return None
+    import oracle
+    nt, nr, nv, ns, nb = w["nt"], w["nr"], w["nv"], w["ns"], w["nb"]
+    p = make_inputs(w, seed=0)
+    D = p.D.astype(np.float32).astype(np.float64)
+    X = np.zeros((nv, nr, nt))
+    U_obs = oracle.mdc_forward_fft(D, p.X_true.astype(np.float32), np.arange(ns))
+    batches = [b for ep in synth.epoch_batches(ns, nb, 2 + (args.steps + args.warmup) // math.ceil(ns / nb),
+                                               seed=0) for b in ep]
+    # per step: a column sample sized so the whole run stays within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    _, _, _, cores = time_oracle(w, D, X, U_obs, [batches], target_s=0.2, max_cols=2)
+    t_tot, f_tot = 0.0, 0.0
+    cols_used = []
+    per_col = None
+    for k in range(args.warmup + args.steps):
+        idx = batches[k]
+        if per_col is None:
+            t0 = time.perf_counter()
+            oracle_step_sample(D, X, U_obs, idx, np.arange(1))
+            per_col = max(time.perf_counter() - t0, 1e-6)
+        ncols = int(max(1, min(nv, budget / per_col)))
+        vsel = np.linspace(0, nv - 1, ncols).round().astype(np.int64)
+        t0 = time.perf_counter()
+        oracle_step_sample(D, X, U_obs, idx, vsel)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            t_tot += dt * nv / ncols
+            f_tot += step_flops(nt, nr, nv, len(idx))
+            cols_used.append(ncols)
+    val = f_tot / t_tot / 1e9
+    sample = (f"each step: FP64 direct-sum forward+adjoint on {min(cols_used)}-{max(cols_used)} of {nv} "
+              f"virtual-source columns, extrapolated linearly in the column count")
+    return {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_tot / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Ricker/hyperbola generator)",
+            "config": {"workload": args.workload, "nt": nt, "nr": nr, "nv": nv, "ns": ns, "nb": nb,
+                       "reciprocity": bool(w["reciprocity"])},
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w = workload_dims(args.workload)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world, w)
+    else:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        out = run_gpu(args, rank, world, w)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -62,7 +62,7 @@ typedef enum { MDC_PREC_FP32 = 0 } mdc_precision;
  *   out     : receives the plan handle (host pointer).
  *   nt      : time samples per trace, 1 <= nt <= 4096.
  *   nr, nv, ns : receivers, virtual sources, sources (>= 1).
- *   nb_max  : largest batch size later passed to any call (1 <= nb_max; 0 means ns).
+ *   nb_max  : largest batch size later passed to any call (1 <= nb_max <= 1024; 0 means ns).
  *   nfft    : FFT length; 0 picks the smallest power of two >= max(2*nt-1, 64).  A non-zero value
  *             must be a power of two >= 2*nt-1 and <= 8192.
  *   scale   : multiplies the operator (the discretisation of the receiver integral in Eq. 1; 1 is a

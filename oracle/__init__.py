@@ -136,7 +136,7 @@ def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None) -> n
     assert nfft >= 2 * nt - 1
     Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
     Xh = np.fft.rfft(X, n=nfft, axis=-1)                            # (nv, nr, nf)
-    Uh = np.einsum("brf,vrf->bvf", Dh, Xh)
+    Uh = np.matmul(Dh.transpose(2, 0, 1), Xh.transpose(2, 1, 0)).transpose(1, 2, 0)   # per f: [nb x nr][nr x nv]
     return scale * np.fft.irfft(Uh, n=nfft, axis=-1)[..., :nt]
 
 
@@ -148,7 +148,7 @@ def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None) -> n
     assert nfft >= 2 * nt - 1
     Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
     Rh = np.fft.rfft(R, n=nfft, axis=-1)                            # (nb, nv, nf)
-    Gh = np.einsum("bvf,brf->vrf", Rh, np.conj(Dh))
+    Gh = np.matmul(Rh.transpose(2, 1, 0), np.conj(Dh).transpose(2, 0, 1)).transpose(1, 2, 0)  # per f: [nv x nb][nb x nr]
     return scale * np.fft.irfft(Gh, n=nfft, axis=-1)[..., :nt]
 
 

@@ -42,7 +42,7 @@ struct mdc_plan_s {
     float2 *Dh = nullptr;        // [nf][ns][ldr]
     float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
     float2 *Uh = nullptr;        // [nf][nv][ldb]  batch spectra (prediction, then residual)
-    float2 *twM = nullptr;       // [M]
+    float2 *tw = nullptr;        // per-pass twiddle tables, tw_size(M) entries
     float2 *twN = nullptr;       // [M+1]
     double *partials = nullptr;  // residual-kernel block partials
     double *lam = nullptr;       // [nf] power-iteration results, [nf] = max
@@ -97,7 +97,7 @@ FftArgs base_fft(const mdc_plan_s *p) {
     FftArgs a;
     memset(&a, 0, sizeof(a));
     a.nt = p->nt;
-    a.twM = p->twM;
+    a.tw = p->tw;
     a.twN = p->twN;
     a.s = p->scale / (float)p->nfft;
     a.status = p->status;
@@ -111,7 +111,6 @@ int ti_log2_for(int n_contig, int TR) {
     return l;
 }
 
-int traces_per_cta(int M) { return M <= 512 ? 16 : 8192 / M; }
 
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
@@ -120,7 +119,7 @@ TraceGrid model_grid(const mdc_plan_s *p, int nouter) {
     TraceGrid g;
     g.ni = p->nr;
     g.nj = nouter;
-    g.ti_log2 = ti_log2_for(p->nr, traces_per_cta(p->M));
+    g.ti_log2 = ti_log2_for(p->nr, fft_traces_per_cta(p->M));
     g.tsi = p->nt;
     g.tsj = (long long)p->nr * p->nt;
     g.ssi = 1;
@@ -134,7 +133,7 @@ TraceGrid batch_grid(const mdc_plan_s *p, int nb) {
     TraceGrid g;
     g.ni = nb;
     g.nj = p->nv;
-    g.ti_log2 = ti_log2_for(nb, traces_per_cta(p->M));
+    g.ti_log2 = ti_log2_for(nb, fft_traces_per_cta(p->M));
     g.tsi = (long long)p->nv * p->nt;
     g.tsj = p->nt;
     g.ssi = 1;
@@ -230,6 +229,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         return MDC_ERR_UNSUPPORTED;
     }
     if (nb_max == 0) nb_max = ns;
+    if (nb_max > 1024) return MDC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
 
     mdc_plan_s *p = new (std::nothrow) mdc_plan_s();
@@ -250,7 +250,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         p->resid_blocks_max = fft_blocks(M, g);
     }
     bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
-              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->twM, M * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)fft_tw_size(M) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->twN, (M + 1) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->partials, (size_t)(p->resid_blocks_max + 1) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&p->lam, (size_t)(nf + 1) * sizeof(double)) == cudaSuccess &&
@@ -261,15 +261,12 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         mdc_plan_destroy(p);
         return MDC_ERR_OOM;
     }
-    // twiddles in double precision, rounded once to float
-    std::vector<float2> tw(M + 1);
+    // per-pass twiddle tables in double precision, rounded once to float
     const double pi = 3.14159265358979323846;
-    for (int m = 0; m < M; ++m) {
-        const double ang = 2.0 * pi * (double)m / (double)M;
-        tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
-    }
+    std::vector<float2> tw;
+    fft_tw_fill(M, tw);
     int rc = MDC_OK;
-    if (cudaMemcpyAsync(p->twM, tw.data(), M * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
     std::vector<float2> twn(M + 1);
     for (int k = 0; k <= M; ++k) {
         const double ang = 2.0 * pi * (double)k / (double)nfft;
@@ -310,7 +307,7 @@ int mdc_plan_destroy(mdc_plan_t p) {
     cudaFree(p->Dh);
     cudaFree(p->Xh);
     cudaFree(p->Uh);
-    cudaFree(p->twM);
+    cudaFree(p->tw);
     cudaFree(p->twN);
     cudaFree(p->partials);
     cudaFree(p->lam);

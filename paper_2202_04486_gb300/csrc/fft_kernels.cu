@@ -6,14 +6,20 @@
 // Appendix A: MDC = FFT along time -> batched per-frequency products -> inverse FFT.  The causal
 // window keeps t in [0, nt) of the length-N result; with N >= 2 nt - 1 this equals the linear
 // convolution (forward) and the linear cross-correlation at non-negative lags (adjoint, Eq. 6).
+//
+// Memory behaviour: a CTA owns TR traces whose spectra are adjacent along the contiguous axis, so a
+// frequency row of the tile is one contiguous segment of TR complex values.  Every thread of the tile
+// loader is bound to one trace and issues all of its P global loads before any shared-memory store;
+// time-domain inputs needed after an inverse FFT (the model for the update, the observed data for the
+// residual) are loaded into registers before that FFT starts, so their latency overlaps the passes.
+#include <cmath>
+#include <vector>
+
 #include "smdd_fft.cuh"
 #include "smdd_internal.h"
 
 namespace smdd {
 
-// ------------------------------------------------------------------------------------------------
-// tile <-> shared memory
-// ------------------------------------------------------------------------------------------------
 struct TileCoord {
     int i, j;
     bool valid;
@@ -33,76 +39,121 @@ __device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr) {
     return c;
 }
 
-// spectra of the CTA's traces -> shared memory (slot 0 of each trace holds (Re X[0], Re X[M]))
+// Spectra of the CTA's traces -> shared memory.  Slot 0 of each trace holds (Re X[0], Re X[M]).
+// Thread binding: trace tr = tid % TR, bins f = tid / TR + it * T (it < P), plus f = M for tid < TR.
 template <int M>
 __device__ __forceinline__ void tile_load_spec(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g) {
-    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE;
-    for (int e = threadIdx.x; e < (M + 1) * TR; e += blockDim.x) {
-        const int f = e / TR, tr = e % TR;
-        const TileCoord c = coord_of<M>(g, tr);
-        float2 v = make_float2(0.f, 0.f);
-        if (c.valid) v = spec[(long long)f * g.ssf + (long long)c.i * g.ssi + (long long)c.j * g.ssj];
-        float2 *b = sm + tr * STR;
-        if (f == 0) reinterpret_cast<float *>(b)[0] = v.x;
-        else if (f == M) reinterpret_cast<float *>(b)[1] = v.x;
-        else b[swz(f)] = v;
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord c = coord_of<M>(g, tr);
+    float2 v[P];
+    float nyq = 0.f;
+    if (c.valid) {
+        const float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
+#pragma unroll
+        for (int it = 0; it < P; ++it) v[it] = __ldcs(s + (long long)(f0 + it * T) * g.ssf);
+        if (f0 == 0) nyq = __ldcs(s + (long long)M * g.ssf).x;
+    } else {
+#pragma unroll
+        for (int it = 0; it < P; ++it) v[it] = make_float2(0.f, 0.f);
+    }
+    float2 *b = sm + tr * STR;
+#pragma unroll
+    for (int it = 0; it < P; ++it) {
+        const int f = f0 + it * T;
+        if (f == 0) b[0] = make_float2(v[it].x, nyq);
+        else b[padi(f)] = v[it];
     }
 }
 
 template <int M>
 __device__ __forceinline__ void tile_store_spec(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g) {
-    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE;
-    for (int e = threadIdx.x; e < (M + 1) * TR; e += blockDim.x) {
-        const int f = e / TR, tr = e % TR;
-        const TileCoord c = coord_of<M>(g, tr);
-        if (!c.valid) continue;
-        const float2 *b = sm + tr * STR;
-        float2 v;
-        if (f == 0) v = make_float2(b[0].x, 0.f);
-        else if (f == M) v = make_float2(b[0].y, 0.f);
-        else v = b[swz(f)];
-        spec[(long long)f * g.ssf + (long long)c.i * g.ssi + (long long)c.j * g.ssj] = v;
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord c = coord_of<M>(g, tr);
+    if (!c.valid) return;
+    const float2 *b = sm + tr * STR;
+    float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
+#pragma unroll
+    for (int it = 0; it < P; ++it) {
+        const int f = f0 + it * T;
+        const float2 v = (f == 0) ? make_float2(b[0].x, 0.f) : b[padi(f)];
+        s[(long long)f * g.ssf] = v;
     }
+    if (f0 == 0) s[(long long)M * g.ssf] = make_float2(b[0].y, 0.f);
 }
 
-// time trace -> registers in first-forward-pass order; samples past nt are the zero padding
+// Time samples for the first-forward-pass positions: register pair (2qq, 2qq+1) x r holds
+// z[n], z[n+1] = (x[2n], x[2n+1]), (x[2n+2], x[2n+3]) with n = 2t + 2T qq + r M/R_1.  Only r < R_1/2 can
+// hold samples (the upper half is the zero padding since nt <= M).  Slot h = qq * (R_1/2) + r.
+constexpr int NPAIR = FFT_P / 4;   // float4 slots per thread
+
 template <int M>
-__device__ __forceinline__ void load_time(const float *__restrict__ x, int nt, bool valid, bool vec, int t,
-                                          float2 (&a)[16]) {
-    constexpr int R = fft_radix(M, 0), T = M / 16, Q = 16 / R, S = M / R;
+__device__ __forceinline__ void load_pairs(const float *__restrict__ x, int nt, bool valid, bool vec, int t,
+                                           float4 (&h)[NPAIR]) {
+    constexpr int R = fft_radix(M, 0), T = M / FFT_P, QQ = FFT_P / R / 2, S = M / R;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
+    for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 v = make_float2(0.f, 0.f);
-            if (r < R / 2 && valid) {   // n < M/2 <= ... ; n >= M/2 holds only padding since nt <= M
-                const int i0 = 2 * (t + T * q + r * S);
-                if (vec) {
-                    if (i0 + 1 < nt) v = *reinterpret_cast<const float2 *>(x + i0);
-                    else if (i0 < nt) v.x = x[i0];
+        for (int r = 0; r < R / 2; ++r) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
+            if (valid) {
+                if (vec && i0 + 3 < nt) {
+                    v = __ldcs(reinterpret_cast<const float4 *>(x + i0));
                 } else {
                     if (i0 < nt) v.x = x[i0];
                     if (i0 + 1 < nt) v.y = x[i0 + 1];
+                    if (i0 + 2 < nt) v.z = x[i0 + 2];
+                    if (i0 + 3 < nt) v.w = x[i0 + 3];
                 }
             }
-            a[q * R + r] = v;
+            h[qq * (R / 2) + r] = v;
         }
+}
+
+// pairs -> first-forward-pass registers (upper half of every butterfly is zero padding)
+template <int M>
+__device__ __forceinline__ void pairs_to_regs(const float4 (&h)[NPAIR], float2 (&a)[FFT_P]) {
+    constexpr int R = fft_radix(M, 0), QQ = FFT_P / R / 2;
+#pragma unroll
+    for (int qq = 0; qq < QQ; ++qq)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 v = (r < R / 2) ? h[qq * (R / 2) + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+            a[(2 * qq) * R + r] = make_float2(v.x, v.y);
+            a[(2 * qq + 1) * R + r] = make_float2(v.z, v.w);
+        }
+}
+
+// write 4 time samples starting at i0 (window [0, nt))
+__device__ __forceinline__ void store_quad(float *y, int i0, int nt, bool vec, float4 v) {
+    if (vec && i0 + 3 < nt) {
+        *reinterpret_cast<float4 *>(y + i0) = v;
+    } else {
+        if (i0 < nt) y[i0] = v.x;
+        if (i0 + 1 < nt) y[i0 + 1] = v.y;
+        if (i0 + 2 < nt) y[i0 + 2] = v.z;
+        if (i0 + 3 < nt) y[i0 + 3] = v.w;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(Team<M>::THREADS) k_rfft(FftArgs a) {
-    extern __shared__ float2 sm[];
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord c = coord_of<M>(a.g, tr);
     float2 *buf = sm + tr * Team<M>::STRIDE;
-    float2 v[16];
+    float4 h[NPAIR];
+    float2 v[FFT_P];
     const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    load_time<M>(x, a.nt, c.valid, a.vec, t, v);
-    fft_forward_regs_to_smem<M>(v, buf, t, a.twM);
+    load_pairs<M>(x, a.nt, c.valid, a.vec, t, h);
+    pairs_to_regs<M>(h, v);
+    fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
     real_post<M>(buf, t, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
@@ -110,31 +161,26 @@ __global__ void __launch_bounds__(Team<M>::THREADS) k_rfft(FftArgs a) {
 
 // spectra -> s * irfft, causal window [0, nt)
 template <int M>
-__global__ void __launch_bounds__(Team<M>::THREADS) k_irfft_out(FftArgs a) {
-    extern __shared__ float2 sm[];
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), Q = 16 / R, S = M / R;
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_irfft_out(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     const TileCoord c = coord_of<M>(a.g, tr);
     float2 *buf = sm + tr * Team<M>::STRIDE;
     real_pre<M>(buf, t, a.twN);
-    float2 v[16];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.twM);
+    float2 v[FFT_P];
+    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
     if (!c.valid) return;   // no barrier follows
     float *y = a.tout + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
+    for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
         for (int r = 0; r < R / 2; ++r) {
-            const int i0 = 2 * (t + T * q + r * S);
-            const float2 z = v[q * R + r];
-            if (a.vec && i0 + 1 < a.nt) {
-                *reinterpret_cast<float2 *>(y + i0) = make_float2(z.x * a.s, z.y * a.s);
-            } else {
-                if (i0 < a.nt) y[i0] = z.x * a.s;
-                if (i0 + 1 < a.nt) y[i0 + 1] = z.y * a.s;
-            }
+            const float2 z0 = v[(2 * qq) * R + r], z1 = v[(2 * qq + 1) * R + r];
+            store_quad(y, 2 * (2 * t + 2 * T * qq + r * S), a.nt, a.vec,
+                       make_float4(z0.x * a.s, z0.y * a.s, z1.x * a.s, z1.y * a.s));
         }
 }
 
@@ -142,6 +188,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();   // red may still be read by a previous call
     if (l == 0) red[w] = v;
     __syncthreads();
     double s = 0.0;
@@ -150,24 +197,28 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;   // valid in thread 0
 }
 
+// four samples starting at i0: z = s * p - o inside the window [0, nt), zero outside
+__device__ __forceinline__ float4 resid_quad(float2 p0, float2 p1, float4 o, float s, int i0, int nt) {
+    float4 z;
+    z.x = (i0 < nt) ? fmaf(p0.x, s, -o.x) : 0.f;
+    z.y = (i0 + 1 < nt) ? fmaf(p0.y, s, -o.y) : 0.f;
+    z.z = (i0 + 2 < nt) ? fmaf(p1.x, s, -o.z) : 0.f;
+    z.w = (i0 + 3 < nt) ? fmaf(p1.y, s, -o.w) : 0.f;
+    return z;
+}
+
 // Residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], loss partial 1/2 sum R^2 (FP64), Rh = rfft(R)
 // written in place over Uh.  Trace grid: i = batch entry b, j = virtual source v.
 template <int M>
-__global__ void __launch_bounds__(Team<M>::THREADS) k_residual(FftArgs a) {
-    extern __shared__ float2 sm[];
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[32];
     __shared__ bool am_last;
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), Q = 16 / R, S = M / R;
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    tile_load_spec<M>(sm, a.spec, a.g);
-    __syncthreads();
     const TileCoord c = coord_of<M>(a.g, tr);
-    float2 *buf = sm + tr * Team<M>::STRIDE;
-    real_pre<M>(buf, t, a.twN);
-    float2 v[16];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.twM);
 
-    // observed row for this trace
+    // observed row for this trace, prefetched before the transforms
     const float *uo = nullptr;
     if (c.valid) {
         int row = c.i;
@@ -180,31 +231,34 @@ __global__ void __launch_bounds__(Team<M>::THREADS) k_residual(FftArgs a) {
         }
         if (row >= 0) uo = a.uobs + (long long)row * a.uo_si + (long long)c.j * a.uo_sj;
     }
+    float4 o[NPAIR];
+    load_pairs<M>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o);
+
+    tile_load_spec<M>(sm, a.spec, a.g);
+    __syncthreads();
+    float2 *buf = sm + tr * Team<M>::STRIDE;
+    real_pre<M>(buf, t, a.twN);
+    float2 v[FFT_P];
+    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
+
     double l2 = 0.0;
+    float4 z[NPAIR];
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
+    for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 z = make_float2(0.f, 0.f);
-            if (r < R / 2 && c.valid) {
-                const int i0 = 2 * (t + T * q + r * S);
-                const float2 p = v[q * R + r];
-                float2 o = make_float2(0.f, 0.f);
-                if (uo) {
-                    if (a.vec && i0 + 1 < a.nt) o = *reinterpret_cast<const float2 *>(uo + i0);
-                    else {
-                        if (i0 < a.nt) o.x = uo[i0];
-                        if (i0 + 1 < a.nt) o.y = uo[i0 + 1];
-                    }
-                }
-                if (i0 < a.nt) z.x = fmaf(p.x, a.s, -o.x);
-                if (i0 + 1 < a.nt) z.y = fmaf(p.y, a.s, -o.y);
-                l2 += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+        for (int r = 0; r < R / 2; ++r) {
+            const int hs = qq * (R / 2) + r;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c.valid) {
+                q = resid_quad(v[(2 * qq) * R + r], v[(2 * qq + 1) * R + r], o[hs], a.s,
+                               2 * (2 * t + 2 * T * qq + r * S), a.nt);
+                l2 += (double)q.x * q.x + (double)q.y * q.y + (double)q.z * q.z + (double)q.w * q.w;
             }
-            v[q * R + r] = z;
+            z[hs] = q;
         }
+    pairs_to_regs<M>(z, v);
     team_sync<T>();          // every thread of the team has finished reading buf
-    fft_forward_regs_to_smem<M>(v, buf, t, a.twM);
+    fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
     real_post<M>(buf, t, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
@@ -219,53 +273,57 @@ __global__ void __launch_bounds__(Team<M>::THREADS) k_residual(FftArgs a) {
         am_last = (prev == (unsigned)(nblk - 1));
     }
     __syncthreads();
-    if (am_last && threadIdx.x == 0) {
+    if (am_last) {   // block-uniform
         __threadfence();
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += *((volatile double *)&a.partials[b]);
-        if (a.loss) *a.loss = 0.5 * s;
-        *a.counter = 0u;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&a.partials[b]);
+        s = block_sum(s, red);   // fixed assignment and order: deterministic
+        if (threadIdx.x == 0) {
+            if (a.loss) *a.loss = 0.5 * s;
+            *a.counter = 0u;
+        }
     }
 }
 
 // SGD update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g;  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
 template <int M, bool KEEP>
-__global__ void __launch_bounds__(Team<M>::THREADS) k_update(FftArgs a) {
-    extern __shared__ float2 sm[];
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), Q = 16 / R, S = M / R;
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    const TileCoord c = coord_of<M>(a.g, tr);
+    float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
+    float4 xo[NPAIR];
+    load_pairs<M>(x, a.nt, c.valid, a.vec, t, xo);      // model samples, prefetched
+
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
-    const TileCoord c = coord_of<M>(a.g, tr);
     float2 *buf = sm + tr * Team<M>::STRIDE;
     real_pre<M>(buf, t, a.twN);
-    float2 v[16];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.twM);
-    float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    const float as = a.alpha * a.s;
+    float2 v[FFT_P];
+    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
+    const float nas = -a.alpha * a.s;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
+    for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 z = make_float2(0.f, 0.f);
-            if (r < R / 2 && c.valid) {
-                const int i0 = 2 * (t + T * q + r * S);
-                const float2 g = v[q * R + r];
-                if (a.vec && i0 + 1 < a.nt) {
-                    const float2 xo = *reinterpret_cast<const float2 *>(x + i0);
-                    z = make_float2(fmaf(-as, g.x, xo.x), fmaf(-as, g.y, xo.y));
-                    *reinterpret_cast<float2 *>(x + i0) = z;
-                } else {
-                    if (i0 < a.nt) { z.x = fmaf(-as, g.x, x[i0]); x[i0] = z.x; }
-                    if (i0 + 1 < a.nt) { z.y = fmaf(-as, g.y, x[i0 + 1]); x[i0 + 1] = z.y; }
-                }
-            }
-            v[q * R + r] = z;
+        for (int r = 0; r < R / 2; ++r) {
+            const int hs = qq * (R / 2) + r;
+            const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
+            const float2 g0 = v[(2 * qq) * R + r], g1 = v[(2 * qq + 1) * R + r];
+            const float4 xv = xo[hs];
+            float4 z;
+            z.x = (i0 < a.nt) ? fmaf(nas, g0.x, xv.x) : 0.f;
+            z.y = (i0 + 1 < a.nt) ? fmaf(nas, g0.y, xv.y) : 0.f;
+            z.z = (i0 + 2 < a.nt) ? fmaf(nas, g1.x, xv.z) : 0.f;
+            z.w = (i0 + 3 < a.nt) ? fmaf(nas, g1.y, xv.w) : 0.f;
+            if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
+            xo[hs] = z;
         }
     if constexpr (KEEP) {
+        pairs_to_regs<M>(xo, v);
         team_sync<T>();
-        fft_forward_regs_to_smem<M>(v, buf, t, a.twM);
+        fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
         real_post<M>(buf, t, a.twN);
         __syncthreads();
         tile_store_spec<M>(sm, a.spec, a.g);
@@ -275,8 +333,8 @@ __global__ void __launch_bounds__(Team<M>::THREADS) k_update(FftArgs a) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-#define SMDD_SWITCH_M(M_, ...)              \
-    switch (M_) {                            \
+#define SMDD_SWITCH_M(M_, ...)                                    \
+    switch (M_) {                                                 \
         case 32: { constexpr int MM = 32; __VA_ARGS__; } break;     \
         case 64: { constexpr int MM = 64; __VA_ARGS__; } break;     \
         case 128: { constexpr int MM = 128; __VA_ARGS__; } break;   \
@@ -285,13 +343,27 @@ __global__ void __launch_bounds__(Team<M>::THREADS) k_update(FftArgs a) {
         case 1024: { constexpr int MM = 1024; __VA_ARGS__; } break; \
         case 2048: { constexpr int MM = 2048; __VA_ARGS__; } break; \
         case 4096: { constexpr int MM = 4096; __VA_ARGS__; } break; \
-        default: return cudaErrorInvalidValue;               \
+        default: return cudaErrorInvalidValue;                    \
     }
 
 template <int M>
 static int blocks_for(const TraceGrid &g) {
     const int ti = 1 << g.ti_log2, tj = Team<M>::TR >> g.ti_log2;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
+}
+
+int fft_traces_per_cta(int M) {
+    switch (M) {
+        case 32: return Team<32>::TR;
+        case 64: return Team<64>::TR;
+        case 128: return Team<128>::TR;
+        case 256: return Team<256>::TR;
+        case 512: return Team<512>::TR;
+        case 1024: return Team<1024>::TR;
+        case 2048: return Team<2048>::TR;
+        case 4096: return Team<4096>::TR;
+    }
+    return 0;
 }
 
 int fft_blocks(int M, const TraceGrid &g) {
@@ -306,6 +378,34 @@ int fft_blocks(int M, const TraceGrid &g) {
         case 4096: return blocks_for<4096>(g);
     }
     return 0;
+}
+
+int fft_tw_size(int M) {
+    switch (M) {
+        case 32: return tw_size(32);
+        case 64: return tw_size(64);
+        case 128: return tw_size(128);
+        case 256: return tw_size(256);
+        case 512: return tw_size(512);
+        case 1024: return tw_size(1024);
+        case 2048: return tw_size(2048);
+        case 4096: return tw_size(4096);
+    }
+    return 0;
+}
+
+void fft_tw_fill(int M, std::vector<float2> &tw) {
+    const double pi = 3.14159265358979323846;
+    tw.assign(fft_tw_size(M) > 0 ? fft_tw_size(M) : 1, make_float2(0.f, 0.f));
+    for (int inv = 0; inv < 2; ++inv)
+        for (int p = 1; p < fft_npass(M); ++p) {
+            const int NS = dir_span(M, inv, p), R = dir_radix(M, inv, p), off = tw_off(M, inv, p);
+            for (int k = 0; k < NS; ++k)
+                for (int r = 0; r < R; ++r) {
+                    const double ang = 2.0 * pi * (double)(r * k) / (double)(NS * R);
+                    tw[off + r * NS + k] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+                }
+        }
 }
 
 cudaError_t fft_prepare(int M) {

@@ -34,18 +34,22 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
 
 // ------------------------------------------------------------------------------------------------
 // forward: C[f][v][b] = sum_r A[f][v][r] * Dh[f][idx_b][r]
-// CTA: 128 threads, 256 rows v (thread t owns rows t and t+128), 16 batch columns, one frequency.
-// K (= nr) streamed in chunks of 16 through a two-stage cp.async pipeline.
+// CTA: 4 warps, 128 rows v x 16 batch columns, one frequency.  Lane (vg = lane & 7, bg = lane >> 3)
+// of warp w owns rows v0 + 32w + vg + 8i and columns b0 + bg + 4j (i, j < 4): a 4 x 4 complex register
+// tile.  K (= nr) streams in chunks of 16 through a two-stage cp.async pipeline; every operand load is
+// 128-bit (two consecutive k) and the 144-byte row pitch puts the 8 distinct rows of a load in 8
+// distinct bank groups.
 // ------------------------------------------------------------------------------------------------
-constexpr int FW_THREADS = 128, FW_ROWS = 256, FW_NB = 16, FW_KC = 16, FW_LD = FW_KC + 2;
+constexpr int FW_THREADS = 128, FW_ROWS = 128, FW_NB = 16, FW_KC = 16, FW_LD = FW_KC + 2;
 constexpr int FW_STAGE = (FW_ROWS + FW_NB) * FW_LD;   // float2 per stage
 constexpr size_t FW_SMEM = 2 * FW_STAGE * sizeof(float2);
 
-__global__ void __launch_bounds__(FW_THREADS) k_cgemm_fwd(GemmArgs a) {
+__global__ void __launch_bounds__(FW_THREADS, 4) k_cgemm_fwd(GemmArgs a) {
     extern __shared__ __align__(16) float2 gsm[];
     const int f = blockIdx.z;
     const int v0 = blockIdx.x * FW_ROWS, b0 = blockIdx.y * FW_NB;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int vg = lane & 7, bg = lane >> 3;
     const float2 *Af = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
 
@@ -89,11 +93,12 @@ __global__ void __launch_bounds__(FW_THREADS) k_cgemm_fwd(GemmArgs a) {
         cp_async_commit();
     };
 
-    float2 acc[2][FW_NB];
+    float2 acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int b = 0; b < FW_NB; ++b) acc[i][b] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    const bool active = v0 + 32 * warp < a.nv;   // warps whose rows all lie past nv skip the products
 
     const int nk = (a.nr + FW_KC - 1) / FW_KC;
     load_stage(0, 0);
@@ -105,19 +110,23 @@ __global__ void __launch_bounds__(FW_THREADS) k_cgemm_fwd(GemmArgs a) {
             cp_async_wait<0>();
         }
         __syncthreads();
-        const float2 *sX = gsm + (kc & 1) * FW_STAGE;
-        const float2 *sD = sX + FW_ROWS * FW_LD;
+        if (active) {
+            const float2 *sX = gsm + (kc & 1) * FW_STAGE + (32 * warp + vg) * FW_LD;
+            const float2 *sD = gsm + (kc & 1) * FW_STAGE + FW_ROWS * FW_LD + bg * FW_LD;
 #pragma unroll
-        for (int kk = 0; kk < FW_KC; kk += 2) {
-            const float4 xa = *reinterpret_cast<const float4 *>(sX + tid * FW_LD + kk);
-            const float4 xb = *reinterpret_cast<const float4 *>(sX + (tid + 128) * FW_LD + kk);
+            for (int kk = 0; kk < FW_KC; kk += 2) {
+                float4 x[4], d[4];
 #pragma unroll
-            for (int b = 0; b < FW_NB; ++b) {
-                const float4 d = *reinterpret_cast<const float4 *>(sD + b * FW_LD + kk);
-                cmac(acc[0][b], make_float2(xa.x, xa.y), make_float2(d.x, d.y));
-                cmac(acc[0][b], make_float2(xa.z, xa.w), make_float2(d.z, d.w));
-                cmac(acc[1][b], make_float2(xb.x, xb.y), make_float2(d.x, d.y));
-                cmac(acc[1][b], make_float2(xb.z, xb.w), make_float2(d.z, d.w));
+                for (int i = 0; i < 4; ++i) x[i] = *reinterpret_cast<const float4 *>(sX + 8 * i * FW_LD + kk);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d[j] = *reinterpret_cast<const float4 *>(sD + 4 * j * FW_LD + kk);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        cmac(acc[i][j], make_float2(x[i].x, x[i].y), make_float2(d[j].x, d[j].y));
+                        cmac(acc[i][j], make_float2(x[i].z, x[i].w), make_float2(d[j].z, d[j].w));
+                    }
             }
         }
         __syncthreads();
@@ -125,15 +134,13 @@ __global__ void __launch_bounds__(FW_THREADS) k_cgemm_fwd(GemmArgs a) {
 
     float2 *Cf = a.C + (long long)f * a.sCf;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int v = v0 + tid + 128 * i;
+    for (int i = 0; i < 4; ++i) {
+        const int v = v0 + 32 * warp + vg + 8 * i;
         if (v >= a.nv) continue;
-        float2 *crow = Cf + (long long)v * a.ldb;
 #pragma unroll
-        for (int b = 0; b < FW_NB; b += 2) {
-            if (b0 + b < a.nb)   // ldb is even, so column b0+b+1 exists (padding when == nb)
-                *reinterpret_cast<float4 *>(crow + b0 + b) =
-                    make_float4(acc[i][b].x, acc[i][b].y, acc[i][b + 1].x, acc[i][b + 1].y);
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + bg + 4 * j;
+            if (b < a.nb) Cf[(long long)v * a.ldb + b] = acc[i][j];
         }
     }
 }
@@ -142,17 +149,70 @@ __global__ void __launch_bounds__(FW_THREADS) k_cgemm_fwd(GemmArgs a) {
 // adjoint: C[f][v][r] = outscale * sum_k A'[v][k] B'[k][r]
 //   k < nb :  A' = Rh[f][v][k],            B' = conj(Dh[f][idx_k][r])
 //   k >= nb (reciprocity only, k' = k - nb):  A' = conj(Dh[f][idx_k'][v]),  B' = Rh[f][r][k']
-// CTA: 128 threads, tile 64 v x 64 r, warp w owns rows 16w..16w+15, lane owns columns lane, lane+32.
+// CTA: 8 warps, tile 64 v x 64 r.  Lane (vp = lane >> 4, rg = lane & 15) of warp w owns rows
+// v0 + 8w + 4vp + {0,1,2,3} and columns r0 + {2rg, 2rg+1, 2rg+32, 2rg+33}.  The operands are staged
+// by cp.async in the layout they have in global memory -- residual-spectrum rows [v][k] and
+// kernel-spectrum rows [k][r] -- and conjugated when used; chunks of 16 k per half.
 // ------------------------------------------------------------------------------------------------
-constexpr int AD_THREADS = 128, AD_T = 64, AD_KC = 16;
-constexpr size_t AD_SMEM_OPER = 2 * AD_KC * AD_T * sizeof(float2);
+constexpr int AD_THREADS = 256, AD_T = 64, AD_KC = 16, AD_LDR = AD_KC + 2, AD_MAXNB = 1024;
+constexpr int AD_RROWS = AD_T * AD_LDR;          // float2: residual rows of one block
+constexpr int AD_DROWS = AD_KC * AD_T;           // float2: kernel rows at one block's columns
+constexpr size_t AD_SMEM_OPER = 2 * (AD_RROWS + AD_DROWS) * sizeof(float2);
 constexpr size_t AD_SMEM_MIRROR = AD_T * (AD_T + 1) * sizeof(float2);
+constexpr size_t AD_SMEM = AD_SMEM_OPER > AD_SMEM_MIRROR ? AD_SMEM_OPER : AD_SMEM_MIRROR;
+
+// stage rows [c0, c0 + 64) x k [k0, k0 + 16) of Rh (row pitch ldb) into s[64][AD_LDR]
+__device__ __forceinline__ void stage_rrows(float2 *s, const float2 *Rf, int ldb, int c0, int nc, int k0, int nb, int tid) {
+#pragma unroll
+    for (int u = 0; u < AD_T * AD_KC / 2 / AD_THREADS; ++u) {
+        const int c = tid + u * AD_THREADS, row = c >> 3, part = c & 7;
+        const int k = k0 + 2 * part;
+        int bytes = 0;
+        const float2 *src = Rf;
+        if (c0 + row < nc && k < nb) {
+            bytes = (k + 1 < nb) ? 16 : 8;
+            src = Rf + (long long)(c0 + row) * ldb + k;
+        }
+        cp_async16(s + row * AD_LDR + 2 * part, src, bytes);
+    }
+}
+
+// stage kernel rows idx[k0 .. k0 + 16) at columns [c0, c0 + 64) into s[16][64]
+__device__ __forceinline__ void stage_drows(float2 *s, const float2 *Df, int ldr, const int *sidx, int c0, int nc, int k0,
+                                            int nb, int tid) {
+#pragma unroll
+    for (int u = 0; u < AD_KC * AD_T / 2 / AD_THREADS; ++u) {
+        const int c = tid + u * AD_THREADS, kk = c >> 5, part = c & 31;
+        const int col = c0 + 2 * part;
+        int bytes = 0;
+        const float2 *src = Df;
+        if (k0 + kk < nb && col < nc) {
+            const int srow = sidx[k0 + kk];
+            if (srow >= 0) {
+                bytes = (col + 1 < nc) ? 16 : 8;
+                src = Df + (long long)srow * ldr + col;
+            }
+        }
+        cp_async16(s + kk * AD_T + 2 * part, src, bytes);
+    }
+}
+
+// acc += a * conj(b)
+__device__ __forceinline__ void cmac_c(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    acc.y = fmaf(-a.x, b.y, acc.y);
+}
 
 template <bool RECIP>
-__global__ void __launch_bounds__(AD_THREADS) k_cgemm_adj(GemmArgs a) {
+__global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
     extern __shared__ __align__(16) float2 gsm[];
-    float2 *sA = gsm;                  // [AD_KC][AD_T]  (k, v)
-    float2 *sB = gsm + AD_KC * AD_T;   // [AD_KC][AD_T]  (k, r)
+    float2 *sRv = gsm;                          // [64][AD_LDR]  Rh rows of the v block
+    float2 *sDr = sRv + AD_RROWS;               // [16][64]      kernel rows at the r block
+    float2 *sRr = sDr + AD_DROWS;               // [64][AD_LDR]  Rh rows of the r block (reciprocity)
+    float2 *sDv = sRr + AD_RROWS;               // [16][64]      kernel rows at the v block (reciprocity)
+    __shared__ int sidx[AD_MAXNB];
     const int f = blockIdx.y;
     int vb, rb;
     if (RECIP) {   // upper-triangular tile enumeration: vb <= rb
@@ -166,67 +226,84 @@ __global__ void __launch_bounds__(AD_THREADS) k_cgemm_adj(GemmArgs a) {
     }
     const int v0 = vb * AD_T, r0 = rb * AD_T;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int vp = lane >> 4, rg = lane & 15;
+    const int vl = 8 * warp + 4 * vp;            // first local row of the thread
     const float2 *Rf = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
-    const int K = RECIP ? 2 * a.nb : a.nb;
 
-    float2 acc[16][2];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-
-    for (int k0 = 0; k0 < K; k0 += AD_KC) {
-        // stage A' (k, v) and B' (k, r)
-        for (int e = tid; e < AD_KC * AD_T; e += AD_THREADS) {
-            // mapping 1: k fastest (rows of Rh are contiguous in k)
-            {
-                const int kk = e % AD_KC, col = e / AD_KC, k = k0 + kk;
-                if (k < a.nb) {
-                    const int v = v0 + col;
-                    sA[kk * AD_T + col] = (v < a.nv) ? Rf[(long long)v * a.ldb + k] : make_float2(0.f, 0.f);
-                } else if (RECIP && k < K) {
-                    const int r = r0 + col;
-                    sB[kk * AD_T + col] = (r < a.nr) ? Rf[(long long)r * a.ldb + (k - a.nb)] : make_float2(0.f, 0.f);
-                }
-            }
-            // mapping 2: column fastest (rows of Dh are contiguous in r / v)
-            {
-                const int col = e % AD_T, kk = e / AD_T, k = k0 + kk;
-                if (k < a.nb) {
-                    const int s = a.idx[k], r = r0 + col;
-                    float2 d = make_float2(0.f, 0.f);
-                    if (s >= 0 && s < a.ns) {
-                        if (r < a.nr) d = cconj(Df[(long long)s * a.ldr + r]);
-                    } else if (col == 0) {
-                        atomicOr(a.status, 1);
-                    }
-                    sB[kk * AD_T + col] = d;
-                } else if (RECIP && k < K) {
-                    const int s = a.idx[k - a.nb], v = v0 + col;
-                    float2 d = make_float2(0.f, 0.f);
-                    if (s >= 0 && s < a.ns && v < a.nv) d = cconj(Df[(long long)s * a.ldr + v]);
-                    sA[kk * AD_T + col] = d;
-                } else if (k >= K) {
-                    sA[kk * AD_T + col] = make_float2(0.f, 0.f);
-                    sB[kk * AD_T + col] = make_float2(0.f, 0.f);
-                }
-            }
+    for (int b = tid; b < a.nb; b += AD_THREADS) {
+        int s = a.idx[b];
+        if (s < 0 || s >= a.ns) {
+            atomicOr(a.status, 1);
+            s = -1;
         }
+        sidx[b] = s;
+    }
+    __syncthreads();
+
+    float2 acc[4][4];   // [row][column: 2rg, 2rg+1, 2rg+32, 2rg+33]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    for (int k0 = 0; k0 < a.nb; k0 += AD_KC) {
+        stage_rrows(sRv, Rf, a.ldb, v0, a.nv, k0, a.nb, tid);
+        stage_drows(sDr, Df, a.ldr, sidx, r0, a.nr, k0, a.nb, tid);
+        if (RECIP) {
+            stage_rrows(sRr, Rf, a.ldb, r0, a.nr, k0, a.nb, tid);
+            stage_drows(sDv, Df, a.ldr, sidx, v0, a.nv, k0, a.nb, tid);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
         __syncthreads();
-        const int kmax = min(AD_KC, K - k0);
-        for (int kk = 0; kk < kmax; ++kk) {
-            const float4 *ap = reinterpret_cast<const float4 *>(sA + kk * AD_T + warp * 16);
-            float2 av[16];
+        const int kn = min(AD_KC, a.nb - k0);
+        // first half: Rh[v][k] * conj(Dh[idx_k][r])
+        for (int kk = 0; kk < kn; kk += 2) {   // kn odd: column kn is zero filled
+            float4 av[4], b0[2], b1[2];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 p = ap[i];
-                av[2 * i] = make_float2(p.x, p.y);
-                av[2 * i + 1] = make_float2(p.z, p.w);
+            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(sRv + (vl + i) * AD_LDR + kk);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                b0[h] = *reinterpret_cast<const float4 *>(sDr + kk * AD_T + 2 * rg + 32 * h);
+                b1[h] = *reinterpret_cast<const float4 *>(sDr + (kk + 1) * AD_T + 2 * rg + 32 * h);
             }
-            const float2 b0 = sB[kk * AD_T + lane], b1 = sB[kk * AD_T + 32 + lane];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                cmac(acc[i][0], av[i], b0);
-                cmac(acc[i][1], av[i], b1);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 a0 = make_float2(av[i].x, av[i].y), a1 = make_float2(av[i].z, av[i].w);
+                    cmac_c(acc[i][2 * h], a0, make_float2(b0[h].x, b0[h].y));
+                    cmac_c(acc[i][2 * h + 1], a0, make_float2(b0[h].z, b0[h].w));
+                    cmac_c(acc[i][2 * h], a1, make_float2(b1[h].x, b1[h].y));
+                    cmac_c(acc[i][2 * h + 1], a1, make_float2(b1[h].z, b1[h].w));
+                }
+        }
+        if (RECIP) {
+            // second half: conj(Dh[idx_k][v]) * Rh[r][k]  (= the transpose of the first half)
+            for (int kk = 0; kk < kn; kk += 2) {
+                float4 d0[2], d1[2], rv[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {   // rows vl + 2h, vl + 2h + 1 at k and k+1
+                    d0[h] = *reinterpret_cast<const float4 *>(sDv + kk * AD_T + vl + 2 * h);
+                    d1[h] = *reinterpret_cast<const float4 *>(sDv + (kk + 1) * AD_T + vl + 2 * h);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int rl = 2 * rg + (j & 1) + 32 * (j >> 1);
+                    rv[j] = *reinterpret_cast<const float4 *>(sRr + rl * AD_LDR + kk);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 dk0 = d0[i >> 1], dk1 = d1[i >> 1];
+                    const float2 c0 = (i & 1) ? make_float2(dk0.z, dk0.w) : make_float2(dk0.x, dk0.y);
+                    const float2 c1 = (i & 1) ? make_float2(dk1.z, dk1.w) : make_float2(dk1.x, dk1.y);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        cmac_c(acc[i][j], make_float2(rv[j].x, rv[j].y), c0);   // Rh[r][k] conj(Dh[k][v])
+                        cmac_c(acc[i][j], make_float2(rv[j].z, rv[j].w), c1);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -235,19 +312,28 @@ __global__ void __launch_bounds__(AD_THREADS) k_cgemm_adj(GemmArgs a) {
     float2 *Cf = a.C + (long long)f * a.sCf;
     const bool diag = RECIP && (vb == rb);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int v = v0 + warp * 16 + i;
+    for (int i = 0; i < 4; ++i) {
+        const int vv = vl + i, v = v0 + vv;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int r = r0 + lane + 32 * h;
-            const float2 val = cscale(acc[i][h], a.outscale);
-            if (v < a.nv && r < a.nr && (!diag || v <= r)) Cf[(long long)v * a.ldr + r] = val;
-            if (RECIP) gsm[(lane + 32 * h) * (AD_T + 1) + warp * 16 + i] = val;   // mirror buffer (r, v)
+            const int rr = 2 * rg + 32 * h, r = r0 + rr;
+            const float2 x0 = cscale(acc[i][2 * h], a.outscale), x1 = cscale(acc[i][2 * h + 1], a.outscale);
+            if (v < a.nv) {
+                const bool w0 = r < a.nr && (!diag || v <= r), w1 = r + 1 < a.nr && (!diag || v <= r + 1);
+                float2 *dst = Cf + (long long)v * a.ldr + r;
+                if (w0 && w1) *reinterpret_cast<float4 *>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+                else {
+                    if (w0) dst[0] = x0;
+                    if (w1) dst[1] = x1;
+                }
+            }
+            if (RECIP) {   // mirror buffer (r, v); operands are dead after the final barrier
+                gsm[rr * (AD_T + 1) + vv] = x0;
+                gsm[(rr + 1) * (AD_T + 1) + vv] = x1;
+            }
         }
     }
     if (RECIP) {
-        // the operand buffers alias the mirror buffer: the K loop ended with a barrier, and the mirror
-        // writes above only start after it
         __syncthreads();
         for (int e = tid; e < AD_T * AD_T; e += AD_THREADS) {
             const int rr = e / AD_T, vv = e % AD_T;
@@ -260,7 +346,7 @@ __global__ void __launch_bounds__(AD_THREADS) k_cgemm_adj(GemmArgs a) {
 cudaError_t gemm_prepare() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_cgemm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM))) return e;
-    const int adj = (int)(AD_SMEM_MIRROR > AD_SMEM_OPER ? AD_SMEM_MIRROR : AD_SMEM_OPER);
+    constexpr int adj = (int)AD_SMEM;
     if ((e = cudaFuncSetAttribute(k_cgemm_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj))) return e;
     if ((e = cudaFuncSetAttribute(k_cgemm_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj))) return e;
     return cudaSuccess;
@@ -278,9 +364,9 @@ cudaError_t launch_cgemm_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_
     a.tiles_r = (a.nr + AD_T - 1) / AD_T;
     if (recip) {
         const int ntiles = a.tiles_v * (a.tiles_v + 1) / 2;
-        k_cgemm_adj<true><<<dim3(ntiles, nf), AD_THREADS, AD_SMEM_MIRROR, st>>>(a);
+        k_cgemm_adj<true><<<dim3(ntiles, nf), AD_THREADS, AD_SMEM, st>>>(a);
     } else {
-        k_cgemm_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), AD_THREADS, AD_SMEM_OPER, st>>>(a);
+        k_cgemm_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), AD_THREADS, AD_SMEM, st>>>(a);
     }
     return cudaGetLastError();
 }

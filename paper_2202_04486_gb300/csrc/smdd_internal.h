@@ -29,7 +29,7 @@ struct FftArgs {
     const float *tin;        // time input (rfft)
     float *tout;             // time output (irfft_out) / model in-out (update)
     float2 *spec;            // spectra (read and/or written)
-    const float2 *twM;       // exp(-2 pi i m / M), m < M
+    const float2 *tw;        // per-pass twiddle tables (see tw_off)
     const float2 *twN;       // exp(-2 pi i k / N), k <= M
     float s;                 // epilogue factor scale / N
     float alpha;             // step size (update)
@@ -62,7 +62,10 @@ cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st);
 cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st);
 cudaError_t launch_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
 int fft_blocks(int M, const TraceGrid &g);
-cudaError_t fft_prepare(int M);   // opt-in to the dynamic shared memory the kernels of size M need
+int fft_traces_per_cta(int M);
+cudaError_t fft_prepare(int M);
+int fft_tw_size(int M);
+void fft_tw_fill(int M, std::vector<float2> &tw);   // host: per-pass twiddle tables   // opt-in to the dynamic shared memory the kernels of size M need
 
 cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
