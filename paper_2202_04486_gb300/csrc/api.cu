@@ -112,7 +112,8 @@ int ti_log2_for(int n_contig, int TR) {
 }
 
 
-bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+// time traces may be read and written as float4: every trace starts on a 16-byte boundary
+bool vec4_ok(int nt, const void *p) { return nt % 4 == 0 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // model-layout grid: trace (i = r, j = v) of a [nv][nr][nt] array  <->  spectra [nf][nv][ldr]
 TraceGrid model_grid(const mdc_plan_s *p, int nouter) {
@@ -146,7 +147,7 @@ int rfft_model(mdc_plan_s *p, const float *X, cudaStream_t st) {
     FftArgs a = base_fft(p);
     a.g = model_grid(p, p->nv);
     a.tin = X;
-    a.vec = (p->nt % 2 == 0) && aligned8(X);
+    a.vec = vec4_ok(p->nt, X);
     a.spec = p->Xh;
     return launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); });
 }
@@ -284,7 +285,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         FftArgs a = base_fft(p);
         a.g = model_grid(p, ns);
         a.tin = D;
-        a.vec = (nt % 2 == 0) && aligned8(D);
+        a.vec = vec4_ok(nt, D);
         a.spec = p->Dh;
         rc = launch_stage(p, ST_SETUP, st, [&] { return launch_rfft(M, a, st); });
     }
@@ -358,7 +359,7 @@ int mdc_forward(mdc_plan_t p, const float *X, const int32_t *idx, int nb, float 
     FftArgs a = base_fft(p);
     a.g = batch_grid(p, nb);
     a.tout = U;
-    a.vec = (p->nt % 2 == 0) && aligned8(U);
+    a.vec = vec4_ok(p->nt, U);
     a.spec = p->Uh;
     return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
 }
@@ -373,7 +374,7 @@ int mdc_adjoint(mdc_plan_t p, const float *R, const int32_t *idx, int nb, float 
         FftArgs a = base_fft(p);
         a.g = batch_grid(p, nb);
         a.tin = R;
-        a.vec = (p->nt % 2 == 0) && aligned8(R);
+        a.vec = vec4_ok(p->nt, R);
         a.spec = p->Uh;
         if ((rc = launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); }))) return rc;
     }
@@ -381,7 +382,7 @@ int mdc_adjoint(mdc_plan_t p, const float *R, const int32_t *idx, int nb, float 
     FftArgs a = base_fft(p);
     a.g = model_grid(p, p->nv);
     a.tout = G;
-    a.vec = (p->nt % 2 == 0) && aligned8(G);
+    a.vec = vec4_ok(p->nt, G);
     a.spec = p->Xh;
     return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
 }
@@ -419,7 +420,7 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         a.gathered = (flags & SMDD_UOBS_GATHERED) ? 1 : 0;
         a.uo_si = (long long)p->nv * p->nt;
         a.uo_sj = p->nt;
-        a.vec = (p->nt % 2 == 0) && aligned8(U_obs);
+        a.vec = vec4_ok(p->nt, U_obs);
         a.partials = p->partials;
         a.counter = p->counter;
         a.loss = loss;
@@ -434,7 +435,7 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         FftArgs a = base_fft(p);
         a.g = model_grid(p, p->nv);
         a.tout = X;
-        a.vec = (p->nt % 2 == 0) && aligned8(X);
+        a.vec = vec4_ok(p->nt, X);
         a.spec = p->Xh;
         a.alpha = prm->alpha;
         if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;

@@ -25,7 +25,7 @@ struct TraceGrid {
 struct FftArgs {
     TraceGrid g;
     int nt;
-    int vec;                 // time traces may be accessed as float2 (nt even, 8-byte aligned)
+    int vec;                 // time traces may be accessed as float4 (nt % 4 == 0, 16-byte aligned base)
     const float *tin;        // time input (rfft)
     float *tout;             // time output (irfft_out) / model in-out (update)
     float2 *spec;            // spectra (read and/or written)

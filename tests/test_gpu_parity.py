@@ -58,6 +58,8 @@ SHAPES = [
     (2500, 3, 2, 4, 2),          # nfft 8192
     (64, 70, 65, 80, 20),        # several 64x64 adjoint tiles, two forward batch tiles
     (16, 300, 260, 10, 3),       # nv > 256: two forward row blocks
+    (6, 4, 3, 5, 2),             # nt = 2 mod 4: traces not 16-byte aligned (scalar time I/O)
+    (130, 9, 11, 12, 7),         # nt = 2 mod 4, nfft 512
 ]
 
 
