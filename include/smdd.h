@@ -121,6 +121,25 @@ typedef struct {
 int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
               const smdd_params *params, double *loss, void *stream);
 
+/* Forward MDC without any device allocation (the paper has no counterpart: this exists for callers
+ * that may not call cudaMalloc/cudaFree -- code whose device memory is owned by another allocator or
+ * pool, or loops that cannot afford an allocation's latency and implicit synchronisation).
+ * Computes the same U as mdc_forward on a plan made with the same nt, nr, nv, ns, scale and D, with
+ * nfft the default length.  Every intermediate lives in one static 64 MiB device array that the library
+ * holds on each device where this function has been used, until the process exits.
+ *   D [ns][nr][nt], X [nv][nr][nt], idx int32[nb], U [nb][nv][nt]: device pointers owned by the caller.
+ *   dev_status: device int (or NULL) set to 1 if an index lies outside [0, ns); the caller zeroes it.
+ *   stream: as elsewhere.
+ * Returns MDC_ERR_UNSUPPORTED, launching nothing, when the intermediates of the problem need more than
+ * the 64 MiB: 8 * (nfft/2+1) * (ns*ldr + nv*ldr + nv*ldb) bytes plus the twiddle tables, with ldr and ldb
+ * nr and nb rounded up to even.
+ * The first call on a device looks up the array's device address (once per device) and must therefore
+ * not be the first call made during a stream capture.  All calls share the array: two calls that can
+ * overlap on the GPU (other streams, other host threads) race with each other and must be serialised
+ * by the caller. */
+int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float *D, const float *X,
+                       const int32_t *idx, int nb, float *U, int *dev_status, void *stream);
+
 /* Wait for all work of this plan's device, then return and clear the device-side status word
  * (MDC_OK or MDC_ERR_INDEX_RANGE). */
 int mdc_plan_sync_status(mdc_plan_t plan);

@@ -35,7 +35,7 @@ MDC_NUM_STAGES = 7
 EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
-    "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count",
+    "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
 )
 
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_plan_stage_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]
     lib.mdc_stage_name.argtypes = [i]
     lib.mdc_stage_name.restype = ctypes.c_char_p
+    lib.mdc_forward_static.argtypes = [i, i, i, i, f, vp, vp, vp, i, vp, vp, vp]
     lib.mdc_plan_launch_count.argtypes = [vp]
     lib.mdc_plan_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
@@ -190,6 +191,20 @@ def mdc_plan_stage_times(plan: int, reset: bool = False) -> dict:
 
 def mdc_plan_launch_count(plan: int) -> int:
     return int(load_library().mdc_plan_launch_count(ctypes.c_void_p(plan)))
+
+
+def mdc_forward_static(D: torch.Tensor, X: torch.Tensor, idx: torch.Tensor, U: torch.Tensor, scale: float = 1.0,
+                       dev_status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Forward MDC through the allocation-free entry point (no plan; intermediates in the library's
+    static device scratch).  Shapes as for mdc_forward; D is [ns][nr][nt]."""
+    _require_cuda()
+    ns, nr, nt = D.shape
+    nv = X.shape[0]
+    st = ctypes.c_void_p(0) if dev_status is None else _dev(dev_status, "dev_status", torch.int32)
+    _check(load_library().mdc_forward_static(nt, nr, nv, ns, float(scale), _dev(D, "D", torch.float32),
+                                             _dev(X, "X", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
+                                             _dev(U, "U", torch.float32), st, _stream_ptr(stream)), "mdc_forward_static")
+    return U
 
 
 # ------------------------------------------------------------------------------------------------
