@@ -153,8 +153,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArg
     const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     load_pairs<M>(x, a.nt, c.valid, a.vec, t, h);
     pairs_to_regs<M>(h, v);
-    fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
-    real_post<M>(buf, t, a.twN);
+    rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
 }
@@ -169,9 +168,8 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_irfft_out(F
     __syncthreads();
     const TileCoord c = coord_of<M>(a.g, tr);
     float2 *buf = sm + tr * Team<M>::STRIDE;
-    real_pre<M>(buf, t, a.twN);
     float2 v[FFT_P];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
+    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
     if (!c.valid) return;   // no barrier follows
     float *y = a.tout + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj;
 #pragma unroll
@@ -237,9 +235,8 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
-    real_pre<M>(buf, t, a.twN);
     float2 v[FFT_P];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
+    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
 
     double l2 = 0.0;
     float4 z[NPAIR];
@@ -258,8 +255,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
         }
     pairs_to_regs<M>(z, v);
     team_sync<T>();          // every thread of the team has finished reading buf
-    fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
-    real_post<M>(buf, t, a.twN);
+    rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
 
@@ -300,9 +296,8 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
-    real_pre<M>(buf, t, a.twN);
     float2 v[FFT_P];
-    fft_inverse_smem_to_regs<M>(v, buf, t, a.tw);
+    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
     const float nas = -a.alpha * a.s;
 #pragma unroll
     for (int qq = 0; qq < QQ; ++qq)
@@ -323,8 +318,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
     if constexpr (KEEP) {
         pairs_to_regs<M>(xo, v);
         team_sync<T>();
-        fft_forward_regs_to_smem<M>(v, buf, t, a.tw);
-        real_post<M>(buf, t, a.twN);
+        rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
         __syncthreads();
         tile_store_spec<M>(sm, a.spec, a.g);
     }

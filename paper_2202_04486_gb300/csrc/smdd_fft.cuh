@@ -163,7 +163,8 @@ struct Team {
     static constexpr int THREADS = T * TR;                    // CTA size
     static constexpr int STRIDE = padi(M) + 2;                // float2 per trace buffer (odd multiple of 16 B)
     static constexpr size_t SMEM = (size_t)TR * STRIDE * sizeof(float2);
-    static constexpr int MINB = SMDD_FFT_MINB * THREADS <= 2048 ? SMDD_FFT_MINB : 2048 / THREADS;
+    // resident CTAs per SM asked of the compiler: never below ~80 registers per thread
+    static constexpr int MINB = (768 / THREADS) < 1 ? 1 : ((768 / THREADS) < SMDD_FFT_MINB ? 768 / THREADS : SMDD_FFT_MINB);
 };
 
 template <int T>
@@ -194,20 +195,43 @@ __device__ __forceinline__ void pass_load(const float2 *buf, int t, float2 (&a)[
         }
 }
 
+// Twiddle powers w^r, r < R, from the loaded w^1 (and w^4 when R = 8): at most three dependent
+// complex products per power (a few ulp), instead of one table load per power.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 w1, float2 w4, float2 (&w)[R]) {
+    w[0] = make_float2(1.f, 0.f);
+    w[1] = w1;
+    if constexpr (R >= 4) {
+        w[2] = cmul(w1, w1);
+        w[3] = cmul(w[2], w1);
+    }
+    if constexpr (R == 8) {
+        w[4] = w4;
+        w[5] = cmul(w4, w1);
+        w[6] = cmul(w4, w[2]);
+        w[7] = cmul(w4, w[3]);
+    }
+}
+
 template <int M, int R, int NS, bool INV, int TWOFF>
 __device__ __forceinline__ void pass_compute(float2 (&a)[FFT_P], int t, const float2 *__restrict__ tw) {
     constexpr int T = M / FFT_P, QQ = FFT_P / R / 2;
 #pragma unroll
     for (int qq = 0; qq < QQ; ++qq) {
         if constexpr (NS > 1) {
-            // butterflies j and j+1 use twiddle columns k0 and k0+1, adjacent in row r of the table
+            // butterflies j and j+1 use twiddle columns k0 and k0+1, adjacent in each row of the table
             const int k0 = (2 * t + 2 * T * qq) & (NS - 1);
+            const float4 v1 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 1 * NS + k0));
+            float4 v4 = v1;
+            if constexpr (R == 8) v4 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 4 * NS + k0));
+            float2 w0[R], w1[R];
+            twiddle_powers<R>(make_float2(v1.x, v1.y), make_float2(v4.x, v4.y), w0);
+            twiddle_powers<R>(make_float2(v1.z, v1.w), make_float2(v4.z, v4.w), w1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const float4 w = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + r * NS + k0));
                 float2 &x0 = a[(2 * qq) * R + r], &x1 = a[(2 * qq + 1) * R + r];
-                x0 = INV ? cmulc(x0, make_float2(w.x, w.y)) : cmul(x0, make_float2(w.x, w.y));
-                x1 = INV ? cmulc(x1, make_float2(w.z, w.w)) : cmul(x1, make_float2(w.z, w.w));
+                x0 = INV ? cmulc(x0, w0[r]) : cmul(x0, w0[r]);
+                x1 = INV ? cmulc(x1, w1[r]) : cmul(x1, w1[r]);
             }
         }
         dftR<R, INV>(&a[(2 * qq) * R]);
@@ -246,10 +270,10 @@ __device__ __forceinline__ void pass_store(float2 *buf, int t, const float2 (&a)
     }
 }
 
-template <int M, bool INV, int p>
+template <int M, bool INV, int p, int PEND>
 __device__ __forceinline__ void passes_from(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw) {
-    // pass p >= 1 of a direction: load, compute, and (except for the last inverse pass) store
-    if constexpr (p < fft_npass(M)) {
+    // passes p .. PEND-1 of a direction: load, compute, and (except for the last inverse pass) store
+    if constexpr (p < PEND) {
         constexpr int R = dir_radix(M, INV, p), NS = dir_span(M, INV, p);
         pass_load<M, R>(buf, t, a);
         if constexpr (!INV) team_sync<M / FFT_P>();
@@ -259,81 +283,179 @@ __device__ __forceinline__ void passes_from(float2 (&a)[FFT_P], float2 *buf, int
             pass_store<M, R, NS>(buf, t, a);
             team_sync<M / FFT_P>();
         }
-        passes_from<M, INV, p + 1>(a, buf, t, tw);
+        passes_from<M, INV, p + 1, PEND>(a, buf, t, tw);
     }
 }
 
-// Forward complex FFT of length M.  Input: registers in first-pass order.  Output: natural order in
-// buf (padded layout).  Ends with a team sync.  No thread of the team may still read buf on entry.
+// w_32^m = exp(-2 pi i m / 32), m in [0, 32): the roots used by the real-spectrum passes
+__device__ __forceinline__ float2 root32(int m) {
+    constexpr float c[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                            0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                            0.19509032201612826785f, 0.0f};   // cos(pi m / 16), m = 0..8
+    m &= 31;
+    const int q = m >> 3, rr = m & 7;
+    float x = c[rr], y = c[8 - rr];        // cos, sin of the angle inside the quadrant
+    float cs, sn;
+    switch (q) {
+        case 0: cs = x; sn = y; break;
+        case 1: cs = -y; sn = x; break;
+        case 2: cs = -x; sn = -y; break;
+        default: cs = y; sn = -x; break;
+    }
+    return make_float2(cs, -sn);
+}
+
+// The butterflies of the last forward pass and of the first inverse pass (radix R, span M/R): thread t
+// owns the pairs u = t + T q (q < 8/R) and, for each, the butterflies ja = u and jb = M/R - u
+// (jb = M/(2R) for u = 0).  The bins k = ja + r M/R and M - k = jb + (R-1-r) M/R then lie in the same
+// thread, so the real-signal post- and pre-processing run in registers.
 template <int M>
-__device__ __forceinline__ void fft_forward_regs_to_smem(float2 (&a)[FFT_P], float2 *buf, int t,
-                                                         const float2 *__restrict__ tw) {
+struct EdgePass {
+    static constexpr int R = fft_radix(M, fft_npass(M) - 1);
+    static constexpr int S = M / R;     // span of the last forward pass = stride of its inputs
+    static constexpr int NP = 8 / R;    // pairs per thread
+};
+
+// Last forward pass + real post-processing.  Input: buf after the other forward passes.  Output: buf
+// holds X[1..M-1] in their slots and (X[0], X[M]) in slot 0.  Ends with a team sync.
+template <int M>
+__device__ __forceinline__ void fwd_last_real(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
+                                              const float2 *__restrict__ twN) {
+    constexpr int T = M / FFT_P, R = EdgePass<M>::R, S = EdgePass<M>::S, NP = EdgePass<M>::NP;
+    constexpr int TWOFF = tw_off(M, false, fft_npass(M) - 1);
+    int ja[NP], jb[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int u = t + T * q;
+        ja[q] = u;
+        jb[q] = u ? S - u : S / 2;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            a[(2 * q) * R + r] = buf[padi(ja[q] + r * S)];
+            a[(2 * q + 1) * R + r] = buf[padi(jb[q] + r * S)];
+        }
+    }
+    team_sync<T>();
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int u = ja[q];
+        float2 *A = &a[(2 * q) * R], *B = &a[(2 * q + 1) * R];
+        // twiddles w_M^{r j}: ja from the table, jb = S - u from w_M^{r S} conj(w_M^{r u}) = w_R^r conj(.)
+        const float2 t1 = __ldg(tw + TWOFF + 1 * S + u);
+        const float2 t4 = (R == 8) ? __ldg(tw + TWOFF + 4 * S + u) : t1;
+        float2 wa[R];
+        twiddle_powers<R>(t1, t4, wa);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            A[r] = cmul(A[r], wa[r]);
+            const float2 wb = u ? cmul(root32(32 * r / R), cconj(wa[r])) : root32(16 * r / R);
+            B[r] = cmul(B[r], wb);
+        }
+        dftR<R, false>(A);
+        dftR<R, false>(B);
+        // X[k] = e - i w_N^k d, e = (Z[k] + conj Z[M-k]) / 2, d = (Z[k] - conj Z[M-k]) / 2
+        const float2 wn = __ldg(twN + u);   // w_N^u
+        float2 xa[R], xb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 za = A[r], zma = u ? B[R - 1 - r] : A[(R - r) % R];
+            const float2 zb = B[r], zmb = u ? A[R - 1 - r] : B[R - 1 - r];
+            const float2 wka = cmul(wn, root32(16 * r / R));                                   // w_N^{u + r S}
+            const float2 wkb = u ? cmul(root32(16 * (r + 1) / R), cconj(wn)) : root32(8 / R + 16 * r / R);
+            const float2 pa = cmul(wka, cscale(csub(za, cconj(zma)), 0.5f));
+            const float2 pb = cmul(wkb, cscale(csub(zb, cconj(zmb)), 0.5f));
+            xa[r] = cadd(cscale(cadd(za, cconj(zma)), 0.5f), mul_mi<false>(pa));
+            xb[r] = cadd(cscale(cadd(zb, cconj(zmb)), 0.5f), mul_mi<false>(pb));
+        }
+        if (u == 0) {   // slot 0 packs X[0] and X[M] = Re Z[0] - Im Z[0]
+            xa[0] = make_float2(xa[0].x, A[0].x - A[0].y);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            buf[padi(ja[q] + r * S)] = xa[r];
+            buf[padi(jb[q] + r * S)] = xb[r];
+        }
+    }
+    team_sync<T>();
+}
+
+// First inverse pass with the real pre-processing: buf holds a real-signal spectrum (slot 0 = (X[0],
+// X[M])).  Forms Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) w_N^{-k}, applies the
+// radix-R inverse butterflies and stores the pass output.  Ends with a team sync.
+template <int M>
+__device__ __forceinline__ void inv_first_real(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ twN) {
+    constexpr int T = M / FFT_P, R = EdgePass<M>::R, S = EdgePass<M>::S, NP = EdgePass<M>::NP;
+    int ja[NP], jb[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int u = t + T * q;
+        ja[q] = u;
+        jb[q] = u ? S - u : S / 2;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            a[(2 * q) * R + r] = buf[padi(ja[q] + r * S)];
+            a[(2 * q + 1) * R + r] = buf[padi(jb[q] + r * S)];
+        }
+    }
+    team_sync<T>();
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int u = ja[q];
+        float2 *A = &a[(2 * q) * R], *B = &a[(2 * q + 1) * R];
+        const float2 s0 = A[0];
+        const float2 xm0 = make_float2(s0.y, 0.f);   // X[M] when u == 0
+        if (u == 0) A[0] = make_float2(s0.x, 0.f);
+        const float2 wn = __ldg(twN + u);
+        float2 za[R], zb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 xa = A[r], xma = u ? B[R - 1 - r] : (r == 0 ? xm0 : A[(R - r) % R]);
+            const float2 xb = B[r], xmb = u ? A[R - 1 - r] : B[R - 1 - r];
+            const float2 wka = cmul(wn, root32(16 * r / R));
+            const float2 wkb = u ? cmul(root32(16 * (r + 1) / R), cconj(wn)) : root32(8 / R + 16 * r / R);
+            const float2 oa = cmulc(csub(xa, cconj(xma)), wka);   // times w_N^{-k}
+            const float2 ob = cmulc(csub(xb, cconj(xmb)), wkb);
+            za[r] = cadd(cadd(xa, cconj(xma)), mul_mi<true>(oa));   // E + i O
+            zb[r] = cadd(cadd(xb, cconj(xmb)), mul_mi<true>(ob));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            A[r] = za[r];
+            B[r] = zb[r];
+        }
+        dftR<R, true>(A);
+        dftR<R, true>(B);
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            sts4(buf + padi(ja[q] * R + r), A[r], A[r + 1]);
+            sts4(buf + padi(jb[q] * R + r), B[r], B[r + 1]);
+        }
+    }
+    team_sync<T>();
+}
+
+// Forward real FFT of length 2M.  Input: registers in first-pass order (time samples).  Output: the
+// real-signal spectrum in buf (slot 0 = (X[0], X[M]), bins 1..M-1 in their slots, padded layout).  Ends
+// with a team sync.  No thread of the team may still read buf on entry.
+template <int M>
+__device__ __forceinline__ void rfft_regs_to_smem(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
+                                                  const float2 *__restrict__ twN) {
     constexpr int R0 = fft_radix(M, 0);
     pass_compute<M, R0, 1, false, 0>(a, t, tw);
     pass_store<M, R0, 1>(buf, t, a);
     team_sync<M / FFT_P>();
-    passes_from<M, false, 1>(a, buf, t, tw);
+    passes_from<M, false, 1, fft_npass(M) - 1>(a, buf, t, tw);
+    fwd_last_real<M>(a, buf, t, tw, twN);
 }
 
-// Inverse complex FFT of length M (unnormalised).  Input: natural order in buf.  Output: registers in
-// first-forward-pass order.  The last pass reads buf: sync the team before writing buf again.
+// Inverse real FFT of length 2M (unnormalised: yields 2M x).  Input: real-signal spectrum in buf.
+// Output: registers in first-forward-pass order (time samples).  The last pass reads buf, so the caller
+// must sync the team before writing buf again.
 template <int M>
-__device__ __forceinline__ void fft_inverse_smem_to_regs(float2 (&a)[FFT_P], float2 *buf, int t,
-                                                         const float2 *__restrict__ tw) {
-    constexpr int R0 = ifft_radix(M, 0);
-    pass_load<M, R0>(buf, t, a);
-    pass_compute<M, R0, 1, true, 0>(a, t, tw);
-    team_sync<M / FFT_P>();
-    pass_store<M, R0, 1>(buf, t, a);
-    team_sync<M / FFT_P>();
-    passes_from<M, true, 1>(a, buf, t, tw);
-}
-
-// After the forward complex FFT (Z in buf, natural order): form the real-input spectrum in place.
-// Bins 1..M-1 in their slots; slot 0 holds (X[0], X[M]) (both real).  Ends with a team sync.
-template <int M>
-__device__ __forceinline__ void real_post(float2 *buf, int t, const float2 *__restrict__ twN) {
-    constexpr int T = M / FFT_P;
-#pragma unroll 2
-    for (int k = t; k <= M / 2; k += T) {
-        if (k == 0) {
-            const float2 z = buf[0];
-            buf[0] = make_float2(z.x + z.y, z.x - z.y);
-            continue;
-        }
-        const int pk = padi(k), pm = padi(M - k);
-        const float2 zk = buf[pk], zm = buf[pm];
-        const float2 e = cscale(cadd(zk, cconj(zm)), 0.5f);
-        const float2 d = cscale(csub(zk, cconj(zm)), 0.5f);
-        const float2 p = cmul(__ldg(&twN[k]), d);
-        buf[pk] = cadd(e, mul_mi<false>(p));                                  // e - i p
-        if (k != M - k) buf[pm] = cadd(cconj(e), mul_mi<false>(cconj(p)));    // conj(e) - i conj(p)
-    }
-    team_sync<T>();
-}
-
-// Before the inverse complex FFT: buf holds a real-signal spectrum (slot 0 = (X[0], X[M]), bins
-// 1..M-1 in their slots).  Forms Z[k] = E + i O with E = X[k] + conj X[M-k],
-// O = (X[k] - conj X[M-k]) w_N^{-k}; the inverse complex FFT of Z then yields N x[2n] + i N x[2n+1].
-// Ends with a team sync.
-template <int M>
-__device__ __forceinline__ void real_pre(float2 *buf, int t, const float2 *__restrict__ twN) {
-    constexpr int T = M / FFT_P;
-#pragma unroll 2
-    for (int k = t; k <= M / 2; k += T) {
-        if (k == 0) {
-            const float2 s = buf[0];
-            buf[0] = make_float2(s.x + s.y, s.x - s.y);
-            continue;
-        }
-        const int pk = padi(k), pm = padi(M - k);
-        const float2 xk = buf[pk], xm = buf[pm];
-        const float2 e = cadd(xk, cconj(xm));
-        const float2 o = cmulc(csub(xk, cconj(xm)), __ldg(&twN[k]));   // times w_N^{-k}
-        buf[pk] = cadd(e, mul_mi<true>(o));                            // e + i o
-        if (k != M - k) buf[pm] = cadd(cconj(e), mul_mi<true>(cconj(o)));
-    }
-    team_sync<T>();
+__device__ __forceinline__ void irfft_smem_to_regs(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
+                                                   const float2 *__restrict__ twN) {
+    inv_first_real<M>(a, buf, t, twN);
+    passes_from<M, true, 1, fft_npass(M)>(a, buf, t, tw);
 }
 
 }  // namespace smdd
