@@ -149,23 +149,35 @@ __global__ void __launch_bounds__(FW_THREADS, 4) k_cgemm_fwd(GemmArgs a) {
 // adjoint: C[f][v][r] = outscale * sum_k A'[v][k] B'[k][r]
 //   k < nb :  A' = Rh[f][v][k],            B' = conj(Dh[f][idx_k][r])
 //   k >= nb (reciprocity only, k' = k - nb):  A' = conj(Dh[f][idx_k'][v]),  B' = Rh[f][r][k']
-// CTA: 8 warps, tile 64 v x 64 r.  Lane (vp = lane >> 4, rg = lane & 15) of warp w owns rows
-// v0 + 8w + 4vp + {0,1,2,3} and columns r0 + {2rg, 2rg+1, 2rg+32, 2rg+33}.  The operands are staged
-// by cp.async in the layout they have in global memory -- residual-spectrum rows [v][k] and
-// kernel-spectrum rows [k][r] -- and conjugated when used; chunks of 16 k per half.
+// CTA tile TT x TT (TT = 64 or 32).  A warp covers 4*VPN rows x TT columns: lane (vp = lane / RG,
+// rg = lane % RG) owns rows v0 + 4*VPN*w + 4vp + {0,1,2,3} and columns r0 + {2rg, 2rg+1, 2rg+TT/2,
+// 2rg+TT/2+1}.  Operands are staged by cp.async in their global layouts -- residual-spectrum rows [v][k]
+// and kernel-spectrum rows [k][r] -- and conjugated when used; chunks of 16 k per half.  Warps whose
+// rows all lie past nv skip the products.
 // ------------------------------------------------------------------------------------------------
-constexpr int AD_THREADS = 256, AD_T = 64, AD_KC = 16, AD_LDR = AD_KC + 2, AD_MAXNB = 1024;
-constexpr int AD_RROWS = AD_T * AD_LDR;          // float2: residual rows of one block
-constexpr int AD_DROWS = AD_KC * AD_T;           // float2: kernel rows at one block's columns
-constexpr size_t AD_SMEM_OPER = 2 * (AD_RROWS + AD_DROWS) * sizeof(float2);
-constexpr size_t AD_SMEM_MIRROR = AD_T * (AD_T + 1) * sizeof(float2);
-constexpr size_t AD_SMEM = AD_SMEM_OPER > AD_SMEM_MIRROR ? AD_SMEM_OPER : AD_SMEM_MIRROR;
+constexpr int AD_KC = 16, AD_LDR = AD_KC + 2, AD_MAXNB = 1024;
 
-// stage rows [c0, c0 + 64) x k [k0, k0 + 16) of Rh (row pitch ldb) into s[64][AD_LDR]
+template <int TT>
+struct AdjGeom {
+    static constexpr int RG = TT / 4;             // lanes along r
+    static constexpr int VPN = 32 / RG;           // lane groups along v
+    static constexpr int WROWS = 4 * VPN;         // rows per warp
+    static constexpr int WARPS = TT / WROWS;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int RROWS = TT * AD_LDR;     // float2: residual rows of one block
+    static constexpr int DROWS = AD_KC * TT;      // float2: kernel rows at one block's columns
+    static constexpr size_t SMEM_OPER = 2 * (RROWS + DROWS) * sizeof(float2);
+    static constexpr size_t SMEM_MIRROR = TT * (TT + 1) * sizeof(float2);
+    static constexpr size_t SMEM = SMEM_OPER > SMEM_MIRROR ? SMEM_OPER : SMEM_MIRROR;
+};
+
+// stage rows [c0, c0 + TT) x k [k0, k0 + 16) of Rh (row pitch ldb) into s[TT][AD_LDR]
+template <int TT>
 __device__ __forceinline__ void stage_rrows(float2 *s, const float2 *Rf, int ldb, int c0, int nc, int k0, int nb, int tid) {
+    constexpr int NT = AdjGeom<TT>::THREADS;
 #pragma unroll
-    for (int u = 0; u < AD_T * AD_KC / 2 / AD_THREADS; ++u) {
-        const int c = tid + u * AD_THREADS, row = c >> 3, part = c & 7;
+    for (int u = 0; u < TT * AD_KC / 2 / NT; ++u) {
+        const int c = tid + u * NT, row = c >> 3, part = c & 7;
         const int k = k0 + 2 * part;
         int bytes = 0;
         const float2 *src = Rf;
@@ -177,12 +189,14 @@ __device__ __forceinline__ void stage_rrows(float2 *s, const float2 *Rf, int ldb
     }
 }
 
-// stage kernel rows idx[k0 .. k0 + 16) at columns [c0, c0 + 64) into s[16][64]
+// stage kernel rows idx[k0 .. k0 + 16) at columns [c0, c0 + TT) into s[16][TT]
+template <int TT>
 __device__ __forceinline__ void stage_drows(float2 *s, const float2 *Df, int ldr, const int *sidx, int c0, int nc, int k0,
                                             int nb, int tid) {
+    constexpr int NT = AdjGeom<TT>::THREADS, PARTS = TT / 2;
 #pragma unroll
-    for (int u = 0; u < AD_KC * AD_T / 2 / AD_THREADS; ++u) {
-        const int c = tid + u * AD_THREADS, kk = c >> 5, part = c & 31;
+    for (int u = 0; u < AD_KC * TT / 2 / NT; ++u) {
+        const int c = tid + u * NT, kk = c / PARTS, part = c % PARTS;
         const int col = c0 + 2 * part;
         int bytes = 0;
         const float2 *src = Df;
@@ -193,7 +207,7 @@ __device__ __forceinline__ void stage_drows(float2 *s, const float2 *Df, int ldr
                 src = Df + (long long)srow * ldr + col;
             }
         }
-        cp_async16(s + kk * AD_T + 2 * part, src, bytes);
+        cp_async16(s + kk * TT + 2 * part, src, bytes);
     }
 }
 
@@ -205,13 +219,14 @@ __device__ __forceinline__ void cmac_c(float2 &acc, float2 a, float2 b) {
     acc.y = fmaf(-a.x, b.y, acc.y);
 }
 
-template <bool RECIP>
-__global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
+template <int TT, bool RECIP>
+__global__ void __launch_bounds__(AdjGeom<TT>::THREADS, TT == 64 ? 3 : 8) k_cgemm_adj(GemmArgs a) {
+    using G = AdjGeom<TT>;
     extern __shared__ __align__(16) float2 gsm[];
-    float2 *sRv = gsm;                          // [64][AD_LDR]  Rh rows of the v block
-    float2 *sDr = sRv + AD_RROWS;               // [16][64]      kernel rows at the r block
-    float2 *sRr = sDr + AD_DROWS;               // [64][AD_LDR]  Rh rows of the r block (reciprocity)
-    float2 *sDv = sRr + AD_RROWS;               // [16][64]      kernel rows at the v block (reciprocity)
+    float2 *sRv = gsm;                  // [TT][AD_LDR]  Rh rows of the v block
+    float2 *sDr = sRv + G::RROWS;       // [16][TT]      kernel rows at the r block
+    float2 *sRr = sDr + G::DROWS;       // [TT][AD_LDR]  Rh rows of the r block (reciprocity)
+    float2 *sDv = sRr + G::RROWS;       // [16][TT]      kernel rows at the v block (reciprocity)
     __shared__ int sidx[AD_MAXNB];
     const int f = blockIdx.y;
     int vb, rb;
@@ -224,14 +239,15 @@ __global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
         vb = blockIdx.x / a.tiles_r;
         rb = blockIdx.x % a.tiles_r;
     }
-    const int v0 = vb * AD_T, r0 = rb * AD_T;
+    const int v0 = vb * TT, r0 = rb * TT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int vp = lane >> 4, rg = lane & 15;
-    const int vl = 8 * warp + 4 * vp;            // first local row of the thread
+    const int vp = lane / G::RG, rg = lane % G::RG;
+    const int vl = G::WROWS * warp + 4 * vp;     // first local row of the thread
+    const bool active = v0 + G::WROWS * warp < a.nv;
     const float2 *Rf = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
 
-    for (int b = tid; b < a.nb; b += AD_THREADS) {
+    for (int b = tid; b < a.nb; b += G::THREADS) {
         int s = a.idx[b];
         if (s < 0 || s >= a.ns) {
             atomicOr(a.status, 1);
@@ -241,67 +257,69 @@ __global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
     }
     __syncthreads();
 
-    float2 acc[4][4];   // [row][column: 2rg, 2rg+1, 2rg+32, 2rg+33]
+    float2 acc[4][4];   // [row][column: 2rg, 2rg+1, 2rg+TT/2, 2rg+TT/2+1]
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
     for (int k0 = 0; k0 < a.nb; k0 += AD_KC) {
-        stage_rrows(sRv, Rf, a.ldb, v0, a.nv, k0, a.nb, tid);
-        stage_drows(sDr, Df, a.ldr, sidx, r0, a.nr, k0, a.nb, tid);
+        stage_rrows<TT>(sRv, Rf, a.ldb, v0, a.nv, k0, a.nb, tid);
+        stage_drows<TT>(sDr, Df, a.ldr, sidx, r0, a.nr, k0, a.nb, tid);
         if (RECIP) {
-            stage_rrows(sRr, Rf, a.ldb, r0, a.nr, k0, a.nb, tid);
-            stage_drows(sDv, Df, a.ldr, sidx, v0, a.nv, k0, a.nb, tid);
+            stage_rrows<TT>(sRr, Rf, a.ldb, r0, a.nr, k0, a.nb, tid);
+            stage_drows<TT>(sDv, Df, a.ldr, sidx, v0, a.nv, k0, a.nb, tid);
         }
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
         const int kn = min(AD_KC, a.nb - k0);
-        // first half: Rh[v][k] * conj(Dh[idx_k][r])
-        for (int kk = 0; kk < kn; kk += 2) {   // kn odd: column kn is zero filled
-            float4 av[4], b0[2], b1[2];
+        if (active) {
+            // first half: Rh[v][k] * conj(Dh[idx_k][r])
+            for (int kk = 0; kk < kn; kk += 2) {   // kn odd: column kn is zero filled
+                float4 av[4], b0[2], b1[2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(sRv + (vl + i) * AD_LDR + kk);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                b0[h] = *reinterpret_cast<const float4 *>(sDr + kk * AD_T + 2 * rg + 32 * h);
-                b1[h] = *reinterpret_cast<const float4 *>(sDr + (kk + 1) * AD_T + 2 * rg + 32 * h);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(sRv + (vl + i) * AD_LDR + kk);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float2 a0 = make_float2(av[i].x, av[i].y), a1 = make_float2(av[i].z, av[i].w);
-                    cmac_c(acc[i][2 * h], a0, make_float2(b0[h].x, b0[h].y));
-                    cmac_c(acc[i][2 * h + 1], a0, make_float2(b0[h].z, b0[h].w));
-                    cmac_c(acc[i][2 * h], a1, make_float2(b1[h].x, b1[h].y));
-                    cmac_c(acc[i][2 * h + 1], a1, make_float2(b1[h].z, b1[h].w));
-                }
-        }
-        if (RECIP) {
-            // second half: conj(Dh[idx_k][v]) * Rh[r][k]  (= the transpose of the first half)
-            for (int kk = 0; kk < kn; kk += 2) {
-                float4 d0[2], d1[2], rv[4];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {   // rows vl + 2h, vl + 2h + 1 at k and k+1
-                    d0[h] = *reinterpret_cast<const float4 *>(sDv + kk * AD_T + vl + 2 * h);
-                    d1[h] = *reinterpret_cast<const float4 *>(sDv + (kk + 1) * AD_T + vl + 2 * h);
+                    b0[h] = *reinterpret_cast<const float4 *>(sDr + kk * TT + 2 * rg + (TT / 2) * h);
+                    b1[h] = *reinterpret_cast<const float4 *>(sDr + (kk + 1) * TT + 2 * rg + (TT / 2) * h);
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int rl = 2 * rg + (j & 1) + 32 * (j >> 1);
-                    rv[j] = *reinterpret_cast<const float4 *>(sRr + rl * AD_LDR + kk);
-                }
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 dk0 = d0[i >> 1], dk1 = d1[i >> 1];
-                    const float2 c0 = (i & 1) ? make_float2(dk0.z, dk0.w) : make_float2(dk0.x, dk0.y);
-                    const float2 c1 = (i & 1) ? make_float2(dk1.z, dk1.w) : make_float2(dk1.x, dk1.y);
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 a0 = make_float2(av[i].x, av[i].y), a1 = make_float2(av[i].z, av[i].w);
+                        cmac_c(acc[i][2 * h], a0, make_float2(b0[h].x, b0[h].y));
+                        cmac_c(acc[i][2 * h + 1], a0, make_float2(b0[h].z, b0[h].w));
+                        cmac_c(acc[i][2 * h], a1, make_float2(b1[h].x, b1[h].y));
+                        cmac_c(acc[i][2 * h + 1], a1, make_float2(b1[h].z, b1[h].w));
+                    }
+            }
+            if (RECIP) {
+                // second half: conj(Dh[idx_k][v]) * Rh[r][k]  (= the transpose of the first half)
+                for (int kk = 0; kk < kn; kk += 2) {
+                    float4 d0[2], d1[2], rv[4];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {   // rows vl + 2h, vl + 2h + 1 at k and k+1
+                        d0[h] = *reinterpret_cast<const float4 *>(sDv + kk * TT + vl + 2 * h);
+                        d1[h] = *reinterpret_cast<const float4 *>(sDv + (kk + 1) * TT + vl + 2 * h);
+                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        cmac_c(acc[i][j], make_float2(rv[j].x, rv[j].y), c0);   // Rh[r][k] conj(Dh[k][v])
-                        cmac_c(acc[i][j], make_float2(rv[j].z, rv[j].w), c1);
+                        const int rl = 2 * rg + (j & 1) + (TT / 2) * (j >> 1);
+                        rv[j] = *reinterpret_cast<const float4 *>(sRr + rl * AD_LDR + kk);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 dk0 = d0[i >> 1], dk1 = d1[i >> 1];
+                        const float2 c0 = (i & 1) ? make_float2(dk0.z, dk0.w) : make_float2(dk0.x, dk0.y);
+                        const float2 c1 = (i & 1) ? make_float2(dk1.z, dk1.w) : make_float2(dk1.x, dk1.y);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            cmac_c(acc[i][j], make_float2(rv[j].x, rv[j].y), c0);   // Rh[r][k] conj(Dh[k][v])
+                            cmac_c(acc[i][j], make_float2(rv[j].z, rv[j].w), c1);
+                        }
                     }
                 }
             }
@@ -316,7 +334,7 @@ __global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
         const int vv = vl + i, v = v0 + vv;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int rr = 2 * rg + 32 * h, r = r0 + rr;
+            const int rr = 2 * rg + (TT / 2) * h, r = r0 + rr;
             const float2 x0 = cscale(acc[i][2 * h], a.outscale), x1 = cscale(acc[i][2 * h + 1], a.outscale);
             if (v < a.nv) {
                 const bool w0 = r < a.nr && (!diag || v <= r), w1 = r + 1 < a.nr && (!diag || v <= r + 1);
@@ -328,17 +346,17 @@ __global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
                 }
             }
             if (RECIP) {   // mirror buffer (r, v); operands are dead after the final barrier
-                gsm[rr * (AD_T + 1) + vv] = x0;
-                gsm[(rr + 1) * (AD_T + 1) + vv] = x1;
+                gsm[rr * (TT + 1) + vv] = x0;
+                gsm[(rr + 1) * (TT + 1) + vv] = x1;
             }
         }
     }
     if (RECIP) {
         __syncthreads();
-        for (int e = tid; e < AD_T * AD_T; e += AD_THREADS) {
-            const int rr = e / AD_T, vv = e % AD_T;
+        for (int e = tid; e < TT * TT; e += G::THREADS) {
+            const int rr = e / TT, vv = e % TT;
             const int r = r0 + rr, v = v0 + vv;
-            if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = gsm[rr * (AD_T + 1) + vv];
+            if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = gsm[rr * (TT + 1) + vv];
         }
     }
 }
@@ -346,9 +364,10 @@ __global__ void __launch_bounds__(AD_THREADS, 3) k_cgemm_adj(GemmArgs a) {
 cudaError_t gemm_prepare() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_cgemm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM))) return e;
-    constexpr int adj = (int)AD_SMEM;
-    if ((e = cudaFuncSetAttribute(k_cgemm_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj))) return e;
-    if ((e = cudaFuncSetAttribute(k_cgemm_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj))) return e;
+    if ((e = cudaFuncSetAttribute(k_cgemm_adj<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjGeom<64>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_cgemm_adj<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjGeom<64>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_cgemm_adj<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjGeom<32>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_cgemm_adj<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjGeom<32>::SMEM))) return e;
     return cudaSuccess;
 }
 
@@ -358,16 +377,24 @@ cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_cgemm_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t st) {
+template <int TT>
+static void launch_adj_tt(const GemmArgs &a0, bool recip, int nf, cudaStream_t st) {
     GemmArgs a = a0;
-    a.tiles_v = (a.nv + AD_T - 1) / AD_T;
-    a.tiles_r = (a.nr + AD_T - 1) / AD_T;
+    a.tiles_v = (a.nv + TT - 1) / TT;
+    a.tiles_r = (a.nr + TT - 1) / TT;
     if (recip) {
         const int ntiles = a.tiles_v * (a.tiles_v + 1) / 2;
-        k_cgemm_adj<true><<<dim3(ntiles, nf), AD_THREADS, AD_SMEM, st>>>(a);
+        k_cgemm_adj<TT, true><<<dim3(ntiles, nf), AdjGeom<TT>::THREADS, AdjGeom<TT>::SMEM, st>>>(a);
     } else {
-        k_cgemm_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), AD_THREADS, AD_SMEM, st>>>(a);
+        k_cgemm_adj<TT, false><<<dim3(a.tiles_v * a.tiles_r, nf), AdjGeom<TT>::THREADS, AdjGeom<TT>::SMEM, st>>>(a);
     }
+}
+
+cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st) {
+    // 32-wide tiles waste less of the (triangular, ragged) output at moderate sizes; 64-wide tiles
+    // re-use each staged operand for twice the products when the matrices are large
+    if (a.nv <= 512 && a.nr <= 512) launch_adj_tt<32>(a, recip, nf, st);
+    else launch_adj_tt<64>(a, recip, nf, st);
     return cudaGetLastError();
 }
 
