@@ -51,11 +51,16 @@ typedef enum {
     MDC_ERR_INDEX_RANGE = 3,   /* a source index outside [0, ns) was seen on the device */
     MDC_ERR_OOM = 4,           /* device allocation failed in mdc_plan_create */
     MDC_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
-    MDC_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+    MDC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (tensor-core products) */
     MDC_ERR_UNSUPPORTED = 7    /* size outside the supported range (nt > 4096, nfft not a power of two) */
 } mdc_status;
 
-typedef enum { MDC_PREC_FP32 = 0 } mdc_precision;
+/* Arithmetic of the per-frequency products (the FFTs are FP32 in both):
+ *   MDC_PREC_FP32   : FP32 FMA on the CUDA cores.
+ *   MDC_PREC_BF16X3 : tensor cores (tcgen05); each FP32 operand is split into BF16 hi + lo and every real
+ *                     product is taken as hi*hi + hi*lo + lo*hi with FP32 accumulation (about 16
+ *                     significant bits per operand; relative L2 error of the operator ~1e-5). */
+typedef enum { MDC_PREC_FP32 = 0, MDC_PREC_BF16X3 = 1 } mdc_precision;
 
 /* Create a plan for one MDD problem and precompute the spectrum of the down-going wavefield
  * (Appendix A: the kernel is transformed once; the per-frequency matrices Dh_f are ns x nr).
@@ -68,7 +73,7 @@ typedef enum { MDC_PREC_FP32 = 0 } mdc_precision;
  *   scale   : multiplies the operator (the discretisation of the receiver integral in Eq. 1; 1 is a
  *             plain sum over receivers).
  *   D       : device pointer, [ns][nr][nt] float32, read during this call only.
- *   precision : MDC_PREC_FP32 (FFTs and complex products in float32).
+ *   precision : MDC_PREC_FP32 or MDC_PREC_BF16X3 (see mdc_precision).
  *   stream  : stream for the precompute; the call returns after it has been enqueued.
  * Allocates about 8*nf*(ns+nv)*nr + 8*nf*nv*nb_max bytes of device memory (nf = nfft/2+1). */
 int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max, int nfft,
@@ -141,7 +146,7 @@ int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float 
                        const int32_t *idx, int nb, float *U, int *dev_status, void *stream);
 
 /* Wait for all work of this plan's device, then return and clear the device-side status word
- * (MDC_OK or MDC_ERR_INDEX_RANGE). */
+ * (MDC_OK, MDC_ERR_INDEX_RANGE, or MDC_ERR_TIMEOUT when a bounded wait of a tensor-core kernel gave up). */
 int mdc_plan_sync_status(mdc_plan_t plan);
 
 /* Human-readable name of a status code (static string). */

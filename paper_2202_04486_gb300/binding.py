@@ -32,6 +32,9 @@ SMDD_UOBS_GATHERED = 8
 
 MDC_NUM_STAGES = 7
 
+MDC_PREC_FP32 = 0
+MDC_PREC_BF16X3 = 1
+
 EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
@@ -213,11 +216,13 @@ def mdc_forward_static(D: torch.Tensor, X: torch.Tensor, idx: torch.Tensor, U: t
 class MDCPlan:
     """Owns one C plan: D is transformed once at construction; the methods wrap the C calls."""
 
-    def __init__(self, D: torch.Tensor, nv: int, nb_max: int = 0, nfft: int = 0, scale: float = 1.0, stream=None):
+    def __init__(self, D: torch.Tensor, nv: int, nb_max: int = 0, nfft: int = 0, scale: float = 1.0, stream=None,
+                 precision: int = MDC_PREC_FP32):
         self.ns, self.nr, self.nt = D.shape
         self.nv = nv
         self.nb_max = nb_max or self.ns
-        self.handle = mdc_plan_create(D, nv, nb_max, nfft, scale, 0, stream)
+        self.precision = precision
+        self.handle = mdc_plan_create(D, nv, nb_max, nfft, scale, precision, stream)
         self.nfft, self.nf = mdc_plan_info(self.handle)
         self.device = D.device
 

@@ -38,6 +38,7 @@ struct mdc_plan_s {
     int device = 0;
     int nt = 0, nr = 0, nv = 0, ns = 0, nbmax = 0, nfft = 0, M = 0, nf = 0;
     int ldr = 0, ldb = 0;
+    int prec = MDC_PREC_FP32;
     float scale = 1.f;
     float2 *Dh = nullptr;        // [nf][ns][ldr]
     float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
@@ -165,6 +166,8 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.sCf = (long long)p->nv * p->ldb;
     g.outscale = 1.f;
     g.status = p->status;
+    if (p->prec == MDC_PREC_BF16X3)
+        return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
 }
 
@@ -181,6 +184,8 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.sCf = (long long)p->nv * p->ldr;
     g.outscale = recip ? 0.5f : 1.f;
     g.status = p->status;
+    if (p->prec == MDC_PREC_BF16X3)
+        return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
     return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st); });
 }
 
@@ -220,7 +225,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     if (!out || !D) return MDC_ERR_INVALID_ARG;
     *out = nullptr;
     if (nt < 1 || nr < 1 || nv < 1 || ns < 1 || nb_max < 0) return MDC_ERR_INVALID_ARG;
-    if (precision != MDC_PREC_FP32) return MDC_ERR_UNSUPPORTED;
+    if (precision != MDC_PREC_FP32 && precision != MDC_PREC_BF16X3) return MDC_ERR_UNSUPPORTED;
     if (!std::isfinite(scale)) return MDC_ERR_INVALID_ARG;
     if (nt > 4096) return MDC_ERR_UNSUPPORTED;
     if (nfft == 0) {
@@ -241,6 +246,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     p->ldr = (nr + 1) & ~1;
     p->ldb = (nb_max + 1) & ~1;
     p->scale = scale;
+    p->prec = precision;
 
     const int M = p->M, nf = p->nf;
     const size_t szD = (size_t)nf * ns * p->ldr * sizeof(float2);
@@ -280,6 +286,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     if (cudaMemsetAsync(p->Xh, 0, szX, st) != cudaSuccess) rc = MDC_ERR_CUDA;
     if (cudaMemsetAsync(p->Uh, 0, szU, st) != cudaSuccess) rc = MDC_ERR_CUDA;
     if (rc == MDC_OK && (fft_prepare(M) != cudaSuccess || gemm_prepare() != cudaSuccess)) rc = MDC_ERR_CUDA;
+    if (rc == MDC_OK && precision == MDC_PREC_BF16X3 && tc_prepare() != cudaSuccess) rc = MDC_ERR_CUDA;
     if (rc == MDC_OK) {
         // kernel spectra: D [ns][nr][nt] -> Dh [nf][ns][ldr] (same layout rule as the model)
         FftArgs a = base_fft(p);
@@ -451,7 +458,7 @@ int mdc_plan_sync_status(mdc_plan_t p) {
     int h = 0;
     if (cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MDC_ERR_CUDA;
     if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return MDC_ERR_CUDA;
-    return h ? MDC_ERR_INDEX_RANGE : MDC_OK;
+    return (h & 2) ? MDC_ERR_TIMEOUT : (h & 1) ? MDC_ERR_INDEX_RANGE : MDC_OK;
 }
 
 int mdc_plan_set_profiling(mdc_plan_t p, int enable) {

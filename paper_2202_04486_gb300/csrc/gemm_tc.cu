@@ -1,0 +1,374 @@
+// Per-frequency complex products on the tensor cores (tcgen05) with split-BF16 operands: the
+// mixed-precision form of the batched MMM of Appendix A (Eq. 2 forward, Eq. 6 adjoint).
+//
+// Every FP32 operand value x is written to shared memory as two BF16 numbers, hi = bf16(x) and
+// lo = bf16(x - hi); a real product is x*y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y (the lo*lo term is
+// dropped), accumulated in FP32 in tensor memory.  A complex product uses the four real products
+// (re*re - im*im, re*im + im*re), the subtraction through the negate-B bit of the instruction
+// descriptor.  So each K-step of 16 issues 12 MMAs of M = 128 rows into two accumulators (re, im).
+//
+// The CUDA threads of a CTA load the FP32 complex spectra (coalesced rows), split them and store the
+// four BF16 planes (re hi, re lo, im hi, im lo) in the 128-byte swizzled layouts of tc_common.cuh;
+// thread 0 issues the MMAs and commits them to an mbarrier; every wait is bounded.  Status bits:
+// 1 = a source index out of range, 2 = a bounded wait gave up.
+#include <cstdint>
+
+#include "smdd_fft.cuh"
+#include "smdd_internal.h"
+#include "tc_common.cuh"
+
+namespace smdd {
+
+constexpr int TC_THREADS = 256;
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// load 8 consecutive complex values row[k .. k+8), zero past n (row may be null: all zero)
+__device__ __forceinline__ void load8(const float2 *row, int k, int n, float2 (&z)[8]) {
+    if (row && k + 7 < n) {
+        const float4 *p = reinterpret_cast<const float4 *>(row + k);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 v = __ldg(p + i);
+            z[2 * i] = make_float2(v.x, v.y);
+            z[2 * i + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = (row && k + i < n) ? row[k + i] : make_float2(0.f, 0.f);
+    }
+}
+
+// store one 16-byte chunk of each plane; planes are `pstride` bytes apart
+__device__ __forceinline__ void store_planes(uint8_t *base, int off, int pstride, const Chunk4 &c) {
+    *reinterpret_cast<uint4 *>(base + off) = c.rh;
+    *reinterpret_cast<uint4 *>(base + pstride + off) = c.rl;
+    *reinterpret_cast<uint4 *>(base + 2 * pstride + off) = c.ih;
+    *reinterpret_cast<uint4 *>(base + 3 * pstride + off) = c.il;
+}
+
+// 12 MMAs of one K-step: acc_re += Ar Br - Ai Bi, acc_im += Ar Bi + Ai Br, each real product split
+// into hi*hi + hi*lo + lo*hi.  a[p], b[p]: descriptors of the planes (re hi, re lo, im hi, im lo).
+__device__ __forceinline__ void mma_complex_split(uint32_t d_re, uint32_t d_im, const uint64_t (&a)[4],
+                                                  const uint64_t (&b)[4], uint32_t idp, uint32_t idn, uint32_t acc) {
+    umma_bf16(d_re, a[0], b[0], idp, acc);
+    umma_bf16(d_re, a[0], b[1], idp, 1);
+    umma_bf16(d_re, a[1], b[0], idp, 1);
+    umma_bf16(d_re, a[2], b[2], idn, 1);
+    umma_bf16(d_re, a[2], b[3], idn, 1);
+    umma_bf16(d_re, a[3], b[2], idn, 1);
+    umma_bf16(d_im, a[0], b[2], idp, acc);
+    umma_bf16(d_im, a[0], b[3], idp, 1);
+    umma_bf16(d_im, a[1], b[2], idp, 1);
+    umma_bf16(d_im, a[2], b[0], idp, 1);
+    umma_bf16(d_im, a[2], b[1], idp, 1);
+    umma_bf16(d_im, a[3], b[0], idp, 1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// forward: C[f][v][b] = sum_r A[f][v][r] Dh[f][idx_b][r]   (M = 128 rows v, N = NB batch columns)
+// K = nr streamed in chunks of 64 through two shared-memory stages.
+// ------------------------------------------------------------------------------------------------
+template <int NB>
+struct TcFwd {
+    static constexpr int A_PLANE = 128 * 128;           // bytes per plane per stage
+    static constexpr int B_PLANE = NB * 128;
+    static constexpr int STAGE = 4 * A_PLANE + 4 * B_PLANE;
+    static constexpr size_t SMEM = 2 * (size_t)STAGE + 1024;
+    static constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : 2 * NB;   // power of two >= 32
+};
+
+template <int NB>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
+    using G = TcFwd<NB>;
+    extern __shared__ uint8_t tc_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int drows[NB];
+    __shared__ int fail;
+    uint8_t *sm = align1024(tc_raw);
+    const int f = blockIdx.z, v0 = blockIdx.x * 128, b0 = blockIdx.y * NB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float2 *Af = a.A + (long long)f * a.sAf;
+    const float2 *Df = a.Dh + (long long)f * a.sDf;
+
+    for (int j = tid; j < NB; j += TC_THREADS) {
+        int s = -1;
+        if (b0 + j < a.nb) {
+            s = a.idx[b0 + j];
+            if (s < 0 || s >= a.ns) {
+                atomicOr(a.status, 1);
+                s = -1;
+            }
+        }
+        drows[j] = s;
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    constexpr uint32_t idp = umma_idesc(128, NB, 0, 0, 0), idn = umma_idesc(128, NB, 0, 0, 1);
+
+    const int nk = (a.nr + 63) / 64;
+    for (int kc = 0; kc < nk; ++kc) {
+        const int s = kc & 1;
+        uint8_t *st = sm + s * G::STAGE;
+        if (kc >= 2 && !mbar_wait_bounded(&bars[s], ((kc - 2) >> 1) & 1)) fail = 1;   // stage s free again
+        // model spectra rows: 128 rows x 8 chunks of 8 complex
+        for (int u = tid; u < 128 * 8; u += TC_THREADS) {
+            const int row = u >> 3, c = u & 7, v = v0 + row;
+            float2 z[8];
+            load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z);
+            store_planes(st, row * 128 + ((c ^ (row & 7)) << 4), G::A_PLANE, split8(z, false));
+        }
+        // gathered kernel rows of the batch
+        for (int u = tid; u < NB * 8; u += TC_THREADS) {
+            const int row = u >> 3, c = u & 7, srow = drows[row];
+            float2 z[8];
+            load8(srow >= 0 ? Df + (long long)srow * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z);
+            store_planes(st + 4 * G::A_PLANE, row * 128 + ((c ^ (row & 7)) << 4), G::B_PLANE, split8(z, false));
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (fail) break;
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                uint64_t ad[4], bd[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    ad[p] = umma_desc(smem_u32(st + p * G::A_PLANE + ks * 32), 16, 1024);
+                    bd[p] = umma_desc(smem_u32(st + 4 * G::A_PLANE + p * G::B_PLANE + ks * 32), 16, 1024);
+                }
+                mma_complex_split(tmem, tmem + NB, ad, bd, idp, idn, (kc > 0 || ks > 0) ? 1u : 0u);
+            }
+            umma_commit(&bars[s]);
+        }
+    }
+    if (!fail) {
+        const int last = nk - 1;
+        if (!mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1)) fail = 1;
+    }
+    tc_fence_after();
+    __syncthreads();
+    const bool ok = !fail;
+    // epilogue: TMEM -> shared staging [128][NB] complex -> coalesced rows of C
+    float2 *out = reinterpret_cast<float2 *>(sm);
+    if (ok && warp < 4) {
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+            float re[16], im[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, re);
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + NB + c0, im);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) out[row * (NB + 1) + c0 + j] = make_float2(re[j], im[j]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (ok) {
+        float2 *Cf = a.C + (long long)f * a.sCf;
+        for (int e = tid; e < 128 * NB; e += TC_THREADS) {
+            const int row = e / NB, j = e % NB, v = v0 + row, b = b0 + j;
+            if (v < a.nv && b < a.nb) Cf[(long long)v * a.ldb + b] = out[row * (NB + 1) + j];
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 2);
+    }
+    if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------------
+// adjoint: C[f][v][r] = outscale * sum_k A'[v][k] B'[k][r] on 128 x 128 tiles, K = nb (chunks of 64):
+//   first half  A' = Rh[f][v][b] (K-major),            B' = conj(Dh[f][idx_b][r]) (N-major)
+//   second half A' = conj(Dh[f][idx_b][v]) (M-major),   B' = Rh[f][r][b] (K-major)   (reciprocity)
+// With reciprocity only the upper-triangular tiles run and the transposed tile is mirrored.
+// ------------------------------------------------------------------------------------------------
+struct TcAdj {
+    static constexpr int PLANE = 128 * 128;             // bytes: 128 rows x 64 k, or 2 atoms x 64 k x 128 B
+    static constexpr int OPER = 8 * PLANE;              // A' and B' planes
+    static constexpr int OUT = 128 * 129 * 8;           // complex staging tile, padded rows
+    static constexpr size_t SMEM = (OUT > OPER ? OUT : OPER) + 1024;
+    static constexpr uint32_t TMEM_COLS = 256;
+};
+
+template <bool RECIP>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_adj(GemmArgs a) {
+    extern __shared__ uint8_t tc_raw[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int sidx[1024];
+    __shared__ int fail;
+    uint8_t *sm = align1024(tc_raw);
+    uint8_t *sA = sm, *sB = sm + 4 * TcAdj::PLANE;
+    const int f = blockIdx.y;
+    int vb, rb;
+    if (RECIP) {
+        int t = blockIdx.x, row = 0, len = a.tiles_v;
+        while (t >= len) { t -= len; ++row; --len; }
+        vb = row;
+        rb = row + t;
+    } else {
+        vb = blockIdx.x / a.tiles_r;
+        rb = blockIdx.x % a.tiles_r;
+    }
+    const int v0 = vb * 128, r0 = rb * 128;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float2 *Rf = a.A + (long long)f * a.sAf;
+    const float2 *Df = a.Dh + (long long)f * a.sDf;
+
+    for (int b = tid; b < a.nb; b += TC_THREADS) {
+        int s = a.idx[b];
+        if (s < 0 || s >= a.ns) {
+            atomicOr(a.status, 1);
+            s = -1;
+        }
+        sidx[b] = s;
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_holder, TcAdj::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    constexpr uint32_t idp1 = umma_idesc(128, 128, 0, 1, 0), idn1 = umma_idesc(128, 128, 0, 1, 1);
+    constexpr uint32_t idp2 = umma_idesc(128, 128, 1, 0, 0), idn2 = umma_idesc(128, 128, 1, 0, 1);
+
+    const int nkc = (a.nb + 63) / 64;
+    const int nhalf = RECIP ? 2 : 1;
+    int phase = 0;
+    for (int kc = 0; kc < nkc && !fail; ++kc) {
+        const int k0 = kc * 64;
+        const int kn = min(64, a.nb - k0), kpad = (kn + 15) & ~15;
+        for (int half = 0; half < nhalf; ++half) {
+            if (kc > 0 || half > 0) {   // the previous MMAs must be done reading the operand planes
+                if (!mbar_wait_bounded(&bar, phase & 1)) fail = 1;
+                ++phase;
+                __syncthreads();
+                if (fail) break;
+            }
+            const int c0 = half ? r0 : v0, nc0 = half ? a.nr : a.nv;   // K-major rows: Rh rows of this block
+            const int c1 = half ? v0 : r0, nc1 = half ? a.nv : a.nr;   // MN-major columns: kernel rows at this block
+            // K-major operand: 128 rows of Rh, k in [k0, k0 + kpad)
+            for (int u = tid; u < 128 * (kpad / 8); u += TC_THREADS) {
+                const int row = u / (kpad / 8), c = u % (kpad / 8), rr = c0 + row;
+                float2 z[8];
+                load8(rr < nc0 ? Rf + (long long)rr * a.ldb : nullptr, k0 + 8 * c, a.nb, z);
+                store_planes(half ? sB : sA, row * 128 + ((c ^ (row & 7)) << 4), TcAdj::PLANE, split8(z, false));
+            }
+            // MN-major operand: kpad rows k of conj(Dh[idx_k]) at 128 columns, 2 atoms of 64
+            for (int u = tid; u < kpad * 16; u += TC_THREADS) {
+                const int k = u >> 4, ch = u & 15, at = ch >> 3, c = ch & 7;
+                const int srow = (k0 + k < a.nb) ? sidx[k0 + k] : -1;
+                float2 z[8];
+                load8(srow >= 0 ? Df + (long long)srow * a.ldr : nullptr, c1 + 64 * at + 8 * c, nc1, z);
+                store_planes(half ? sA : sB, at * (64 * 128) + k * 128 + ((c ^ (k & 7)) << 4), TcAdj::PLANE,
+                             split8(z, true));
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                for (int ks = 0; ks < kpad / 16; ++ks) {
+                    uint64_t ad[4], bd[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        if (!half) {
+                            ad[p] = umma_desc(smem_u32(sA + p * TcAdj::PLANE + ks * 32), 16, 1024);
+                            bd[p] = umma_desc(smem_u32(sB + p * TcAdj::PLANE + ks * 16 * 128), 64 * 128, 1024);
+                        } else {
+                            ad[p] = umma_desc(smem_u32(sA + p * TcAdj::PLANE + ks * 16 * 128), 64 * 128, 1024);
+                            bd[p] = umma_desc(smem_u32(sB + p * TcAdj::PLANE + ks * 32), 16, 1024);
+                        }
+                    }
+                    mma_complex_split(tmem, tmem + 128, ad, bd, half ? idp2 : idp1, half ? idn2 : idn1,
+                                      (kc > 0 || half > 0 || ks > 0) ? 1u : 0u);
+                }
+                umma_commit(&bar);
+            }
+        }
+    }
+    if (!fail && !mbar_wait_bounded(&bar, phase & 1)) fail = 1;
+    tc_fence_after();
+    __syncthreads();
+    const bool ok = !fail;
+    // epilogue: TMEM -> shared staging [128][129] complex -> coalesced rows (and the mirror)
+    float2 *out = reinterpret_cast<float2 *>(sm);
+    if (ok) {
+        const int q = warp & 3, half_cols = warp >> 2;   // warps 0-3: columns 0-63, warps 4-7: 64-127
+        const int row = 32 * q + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            const int col = 64 * half_cols + c0;
+            float re[16], im[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col, re);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128 + col, im);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) out[row * 129 + col + j] = make_float2(re[j] * a.outscale, im[j] * a.outscale);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (ok) {
+        float2 *Cf = a.C + (long long)f * a.sCf;
+        const bool diag = RECIP && vb == rb;
+        for (int e = tid; e < 128 * 128; e += TC_THREADS) {
+            const int row = e >> 7, col = e & 127, v = v0 + row, r = r0 + col;
+            if (v < a.nv && r < a.nr && (!diag || v <= r)) Cf[(long long)v * a.ldr + r] = out[row * 129 + col];
+        }
+        if (RECIP) {
+            for (int e = tid; e < 128 * 128; e += TC_THREADS) {
+                const int rr = e >> 7, vv = e & 127, v = v0 + vv, r = r0 + rr;
+                if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = out[vv * 129 + rr];
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 2);
+    }
+    if (warp == 0) tmem_dealloc(tmem, TcAdj::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------------
+cudaError_t tc_prepare() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
+    const int gx = (a.nv + 127) / 128;
+    if (a.nb <= 16) k_tc_fwd<16><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16>::SMEM, st>>>(a);
+    else if (a.nb <= 32) k_tc_fwd<32><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32>::SMEM, st>>>(a);
+    else k_tc_fwd<64><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64>::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t st) {
+    GemmArgs a = a0;
+    a.tiles_v = (a.nv + 127) / 128;
+    a.tiles_r = (a.nr + 127) / 128;
+    if (recip) k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+    else k_tc_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace smdd

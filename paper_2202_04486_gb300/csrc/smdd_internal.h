@@ -71,6 +71,11 @@ cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
 cudaError_t gemm_prepare();
 
+// split-BF16 tensor-core products (tcgen05)
+cudaError_t tc_prepare();
+cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st);
+cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
+
 cudaError_t launch_power_iter(const float2 *Dh, int ns, int nr, int ldr, long long sDf, int nf, int n_iter,
                               double *lam, cudaStream_t st);
 cudaError_t launch_max_reduce(const double *lam, int n, double *out, cudaStream_t st);
