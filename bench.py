@@ -270,7 +270,8 @@ def run_gpu(args, rank, world, w):
     gen.close()
     del X_true
 
-    plan = binding.MDCPlan(D, nv, nb_max=nb)
+    prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
+    plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
     sigma2 = plan.sigma2_max(60)
     alpha = 0.5 * 2.0 / sigma2
     flags = (binding.SMDD_RECIPROCITY if recip else 0) | binding.SMDD_KEEP_XHAT
@@ -384,7 +385,7 @@ def run_gpu(args, rank, world, w):
     dom = max(st, key=lambda k: st[k][0])
     dom_ms = st[dom][0] / st[dom][1]
     kw = kernel_work(dom, nt, nr, nv, nb)
-    if dom in ("cgemm_fwd", "cgemm_adj"):
+    if dom in ("cgemm_fwd", "cgemm_adj") and args.precision == "fp32":
         peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
         ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
@@ -411,10 +412,11 @@ def run_gpu(args, rank, world, w):
     out = {
         "metric": METRIC, "value": round(flops_all / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
         "data": "synthetic (seeded Ricker/hyperbola generator; U_obs = GPU forward of the true model + 5% noise)",
         "config": {"workload": args.workload, "nt": nt, "nr": nr, "nv": nv, "ns": ns, "nb": nb,
-                   "nfft": nfft_for(nt), "reciprocity": recip, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
+                   "nfft": nfft_for(nt), "reciprocity": recip, "precision": args.precision, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
                    "l2": "flushed before every timed step (256 MiB write, outside the step events)",
                    "per_rank": "independent problem replica, seed = rank (no data-path collective)"},
         "e2e": {"value": round(flops_all / t_e2e / 1e9, 2), "unit": UNIT,
@@ -495,6 +497,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"],
+                    help="arithmetic of the per-frequency products (the FFTs are FP32 in both)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -123,12 +123,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
         const int s = kc & 1;
         uint8_t *st = sm + s * G::STAGE;
         if (kc >= 2 && !mbar_wait_bounded(&bars[s], ((kc - 2) >> 1) & 1)) fail = 1;   // stage s free again
-        // model spectra rows: 128 rows x 8 chunks of 8 complex
-        for (int u = tid; u < 128 * 8; u += TC_THREADS) {
-            const int row = u >> 3, c = u & 7, v = v0 + row;
-            float2 z[8];
-            load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z);
-            store_planes(st, row * 128 + ((c ^ (row & 7)) << 4), G::A_PLANE, split8(z, false));
+        // model spectra rows: 128 rows x 8 chunks of 8 complex; every load of the chunk is issued
+        // before the first split, so their latencies overlap
+        {
+            constexpr int UA = 128 * 8 / TC_THREADS;
+            float2 z[UA][8];
+#pragma unroll
+            for (int i = 0; i < UA; ++i) {
+                const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7, v = v0 + row;
+                load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < UA; ++i) {
+                const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7;
+                store_planes(st, row * 128 + ((c ^ (row & 7)) << 4), G::A_PLANE, split8(z[i], false));
+            }
         }
         // gathered kernel rows of the batch
         for (int u = tid; u < NB * 8; u += TC_THREADS) {
