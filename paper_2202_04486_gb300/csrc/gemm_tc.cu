@@ -20,6 +20,10 @@
 namespace smdd {
 
 constexpr int TC_THREADS = 256;
+#ifndef SMDD_TC_FWD_STAGES
+#define SMDD_TC_FWD_STAGES 1   // one stage: two CTAs share an SM and hide each other's load latency
+#endif
+constexpr int TC_FWD_STAGES = SMDD_TC_FWD_STAGES;
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -71,18 +75,18 @@ __device__ __forceinline__ void mma_complex_split(uint32_t d_re, uint32_t d_im, 
 // forward: C[f][v][b] = sum_r A[f][v][r] Dh[f][idx_b][r]   (M = 128 rows v, N = NB batch columns)
 // K = nr streamed in chunks of 64 through two shared-memory stages.
 // ------------------------------------------------------------------------------------------------
-template <int NB>
+template <int NB, int NSTAGE>
 struct TcFwd {
     static constexpr int A_PLANE = 128 * 128;           // bytes per plane per stage
     static constexpr int B_PLANE = NB * 128;
     static constexpr int STAGE = 4 * A_PLANE + 4 * B_PLANE;
-    static constexpr size_t SMEM = 2 * (size_t)STAGE + 1024;
+    static constexpr size_t SMEM = NSTAGE * (size_t)STAGE + 1024;
     static constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : 2 * NB;   // power of two >= 32
 };
 
-template <int NB>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
-    using G = TcFwd<NB>;
+template <int NB, int NSTAGE>
+__global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(GemmArgs a) {
+    using G = TcFwd<NB, NSTAGE>;
     extern __shared__ uint8_t tc_raw[];
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_holder;
@@ -120,11 +124,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
 
     const int nk = (a.nr + 63) / 64;
     for (int kc = 0; kc < nk; ++kc) {
-        const int s = kc & 1;
+        const int s = kc % NSTAGE;
         uint8_t *st = sm + s * G::STAGE;
-        if (kc >= 2 && !mbar_wait_bounded(&bars[s], ((kc - 2) >> 1) & 1)) fail = 1;   // stage s free again
         // model spectra rows: 128 rows x 8 chunks of 8 complex; every load of the chunk is issued
-        // before the first split, so their latencies overlap
+        // before the first split, so their latencies overlap, and before the wait for the stage, so
+        // they also overlap the MMAs of the previous chunk
         {
             constexpr int UA = 128 * 8 / TC_THREADS;
             float2 z[UA][8];
@@ -133,6 +137,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
                 const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7, v = v0 + row;
                 load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z[i]);
             }
+            // stage s is free again once the MMAs of chunk kc - NSTAGE (the previous use of bars[s]) are done
+            if (kc >= NSTAGE && !mbar_wait_bounded(&bars[s], ((kc - NSTAGE) / NSTAGE) & 1)) fail = 1;
 #pragma unroll
             for (int i = 0; i < UA; ++i) {
                 const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7;
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_fwd(GemmArgs a) {
     }
     if (!fail) {
         const int last = nk - 1;
-        if (!mbar_wait_bounded(&bars[last & 1], (last >> 1) & 1)) fail = 1;
+        if (!mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1)) fail = 1;
     }
     tc_fence_after();
     __syncthreads();
@@ -355,9 +361,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_adj(GemmArgs a) {
 // ------------------------------------------------------------------------------------------------
 cudaError_t tc_prepare() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tc_fwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16>::SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(k_tc_fwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32>::SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(k_tc_fwd<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<16, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<32, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<64, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     return cudaSuccess;
@@ -365,9 +371,10 @@ cudaError_t tc_prepare() {
 
 cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
     const int gx = (a.nv + 127) / 128;
-    if (a.nb <= 16) k_tc_fwd<16><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16>::SMEM, st>>>(a);
-    else if (a.nb <= 32) k_tc_fwd<32><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32>::SMEM, st>>>(a);
-    else k_tc_fwd<64><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64>::SMEM, st>>>(a);
+    constexpr int S = TC_FWD_STAGES;
+    if (a.nb <= 16) k_tc_fwd<16, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16, S>::SMEM, st>>>(a);
+    else if (a.nb <= 32) k_tc_fwd<32, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32, S>::SMEM, st>>>(a);
+    else k_tc_fwd<64, S><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64, S>::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 

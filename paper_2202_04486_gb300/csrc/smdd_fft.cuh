@@ -161,7 +161,9 @@ struct Team {
     static constexpr int TR_RAW = SMDD_FFT_TRACES * 512 / M;  // SMDD_FFT_TRACES traces per CTA at M = 512
     static constexpr int TR = TR_RAW < 2 ? 2 : (T * TR_RAW > 1024 ? 1024 / T : TR_RAW);   // traces per CTA
     static constexpr int THREADS = T * TR;                    // CTA size
-    static constexpr int STRIDE = padi(M) + 2;                // float2 per trace buffer (odd multiple of 16 B)
+    // float2 per trace buffer: padi(M) is a multiple of 16; the extra 16/TR float2 make the TR traces x
+    // 16/TR bins that a half-warp touches in the tile loads / stores fall on 16 distinct bank pairs
+    static constexpr int STRIDE = padi(M) + (TR >= 8 ? 2 : 16 / TR);
     static constexpr size_t SMEM = (size_t)TR * STRIDE * sizeof(float2);
     // resident CTAs per SM asked of the compiler: never below ~80 registers per thread
     static constexpr int MINB = (768 / THREADS) < 1 ? 1 : ((768 / THREADS) < SMDD_FFT_MINB ? 768 / THREADS : SMDD_FFT_MINB);
