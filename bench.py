@@ -272,6 +272,7 @@ def run_gpu(args, rank, world, w):
 
     prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
     plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
+    chosen = plan.autotune(nb, binding.SMDD_RECIPROCITY if recip else 0, reps=5) if args.autotune else plan.get_config()
     sigma2 = plan.sigma2_max(60)
     alpha = 0.5 * 2.0 / sigma2
     flags = (binding.SMDD_RECIPROCITY if recip else 0) | binding.SMDD_KEEP_XHAT
@@ -418,7 +419,8 @@ def run_gpu(args, rank, world, w):
         "config": {"workload": args.workload, "nt": nt, "nr": nr, "nv": nv, "ns": ns, "nb": nb,
                    "nfft": nfft_for(nt), "reciprocity": recip, "precision": args.precision, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
                    "l2": "flushed before every timed step (256 MiB write, outside the step events)",
-                   "per_rank": "independent problem replica, seed = rank (no data-path collective)"},
+                   "per_rank": "independent problem replica, seed = rank (no data-path collective)",
+                   "autotuned": bool(args.autotune), "kernel_config": chosen},
         "e2e": {"value": round(flops_all / t_e2e / 1e9, 2), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches) * world,
@@ -439,6 +441,188 @@ def run_gpu(args, rank, world, w):
         val, t_step, sample, cores = time_oracle(w, D64, Xs, Uo, [batches[args.warmup:]])
         out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": sample, "s_per_step_extrapolated": round(t_step, 3)}
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm, many independent problems: whole epochs of every member replayed from one CUDA graph
+# ------------------------------------------------------------------------------------------------
+BATCH_WORKLOAD = "smdd_batch48_nb32"
+
+
+def run_gpu_batch(args, rank, world):
+    import torch
+
+    from paper_2202_04486_gb300 import binding, build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(binding.LIB_PATH):
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    binding.load_library()
+    specs = synth.batch_members(args.batch_n, seed=1000 + 100000 * rank,
+                                largest=(1500, 1200, 1200, 1200) if args.batch_largest else None)
+    prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
+    n_perm = args.warmup + args.steps
+    members, setup = [], []
+    t_setup = time.perf_counter()
+    for m in specs:
+        nt, nr, nv, ns, nb = m["nt"], m["nr"], m["nv"], m["ns"], m["nb"]
+        D, Xt = synth.make_problem_device(nt, nr, nv, ns, dx=m["dx"], n_reflectors=m["n_reflectors"],
+                                          n_multiples=m["n_multiples"], seed=m["seed"], device=dev)
+        plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
+        U_obs = torch.empty((ns, nv, nt), device=dev)
+        for s0 in range(0, ns, nb):
+            ii = torch.arange(s0, min(ns, s0 + nb), device=dev, dtype=torch.int32)
+            plan.forward(Xt, ii, out=U_obs[s0:s0 + ii.numel()])
+        del D, Xt
+        alpha = 0.5 * 2.0 / plan.sigma2_max(30)
+        flags = binding.SMDD_RECIPROCITY if m["reciprocity"] else 0
+        cfg = plan.autotune(nb, flags, reps=3) if args.autotune else plan.get_config()
+        perm = np.stack([np.concatenate(ep) for ep in synth.epoch_batches(ns, nb, n_perm, seed=m["seed"])])
+        steps = -(-ns // nb)
+        members.append(dict(plan=plan, X=torch.zeros((nv, nr, nt), device=dev), U_obs=U_obs,
+                            perm=torch.from_numpy(perm).to(dev), nb=nb, alpha=alpha, flags=flags,
+                            loss=torch.zeros((n_perm, steps), device=dev, dtype=torch.float64)))
+        setup.append(dict(m, steps=steps, cfg=cfg, perm_host=torch.from_numpy(perm).pin_memory()))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    batch = binding.MDCBatch(members, n_branches=args.branches)
+    epoch_flops = sum(step_flops(m["nt"], m["nr"], m["nv"], min(m["nb"], m["ns"] - s * m["nb"]))
+                      for m in setup for s in range(m["steps"]))
+    stream = torch.cuda.current_stream()
+
+    batch.run(0, args.warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        smi_id = str(local)
+    with ClockSampler(smi_id) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            batch.run(args.warmup + i, 1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    for m in members:
+        st = m["plan"].sync_status()
+        if st != binding.MDC_OK:
+            raise RuntimeError(f"device status {binding.status_string(st)}")
+    t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    launches = (batch.kernels_per_epoch + 1) * args.steps
+    loss_first = [float(m["loss"][0, 0]) for m in members]
+    loss_last = [float(m["loss"][args.warmup + args.steps - 1, -1]) for m in members]
+
+    # e2e: every epoch's permutations go host -> device (pinned) before the replay and every member's
+    # step losses come back device -> host after it
+    loss_host = [torch.empty_like(m["loss"][0], device="cpu").pin_memory() for m in members]
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for i in range(args.steps):
+        e = args.warmup + i
+        for m, sp in zip(members, setup):
+            m["perm"][e % n_perm].copy_(sp["perm_host"][e % n_perm], non_blocking=True)
+            h2d += sp["perm_host"][0].numel() * 4
+        batch.run(e, 1)
+        for m, lh in zip(members, loss_host):
+            lh.copy_(m["loss"][e % n_perm], non_blocking=True)
+            d2h += lh.numel() * 8
+        stream.synchronize()
+    t_e2e = time.perf_counter() - e0
+
+    # dominant kernel of the largest member, from a few profiled steps outside the graph
+    big = max(range(len(setup)), key=lambda k: step_flops(setup[k]["nt"], setup[k]["nr"], setup[k]["nv"], setup[k]["nb"]))
+    mb, sb = members[big], setup[big]
+    plan = mb["plan"]
+    binding.mdc_plan_set_profiling(plan.handle, True)
+    binding.mdc_plan_stage_times(plan.handle, reset=True)
+    for s in range(3):
+        ii = mb["perm"][0, s * sb["nb"]:(s + 1) * sb["nb"]]
+        binding.smdd_step(plan.handle, mb["X"], mb["U_obs"], ii, mb["alpha"],
+                          mb["flags"] | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if s else 0))
+    stage = binding.mdc_plan_stage_times(plan.handle, reset=True)
+    binding.mdc_plan_set_profiling(plan.handle, False)
+    peaks, peak_src = load_peaks()
+    st = {k: v for k, v in stage.items() if v[1] > 0 and k in ("cgemm_fwd", "residual", "cgemm_adj", "update")}
+    dom = max(st, key=lambda k: st[k][0] / st[k][1])
+    dom_ms = st[dom][0] / st[dom][1]
+    kw = kernel_work(dom, sb["nt"], sb["nr"], sb["nv"], sb["nb"])
+    if dom in ("cgemm_fwd", "cgemm_adj") and args.precision == "bf16x3":
+        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
+        pk = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+        roof = {"bound": "tensor", "achieved": round(ach, 2), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
+                "traffic": None, "kernel": dom,
+                "peak_source": f"{peak_src} bf16 sustained (algorithmic complex flops, not the 9 split products)"}
+    elif dom in ("cgemm_fwd", "cgemm_adj"):
+        props = torch.cuda.get_device_properties(dev)
+        pk = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(pk, 2), "unit": "TFLOP/s",
+                "frac": round(ach / pk, 4), "traffic": None, "kernel": dom, "peak_source": "derived FP32 SIMT peak"}
+    else:
+        pk = float(peaks["hbm_gbs"])
+        ach = kw["bytes"] / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
+                "traffic": None, "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof["launch_ms"] = round(dom_ms, 4)
+    roof["member"] = {k: sb[k] for k in ("nt", "nr", "nv", "ns", "nb")}
+    roof["stage_ms_per_launch"] = {k: round(v[0] / v[1], 4) for k, v in st.items()}
+
+    tt = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device=dev)
+    ff = torch.tensor([epoch_flops * args.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(ff, op=torch.distributed.ReduceOp.SUM)
+    t_dev, t_e2e, wall = tt.tolist()
+    if rank != 0:
+        return None
+    cfgs = {}
+    for sp in setup:
+        key = f"fft{sp['cfg']['fft_variant']}_fwd{sp['cfg']['gemm_fwd']}_adj{sp['cfg']['gemm_adj']}"
+        cfgs[key] = cfgs.get(key, 0) + 1
+    out = {
+        "metric": METRIC, "value": round(ff.item() / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_dev / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
+        "data": "synthetic (seeded Ricker/hyperbola generator per member, evaluated on the device; U_obs = GPU forward)",
+        "config": {"workload": BATCH_WORKLOAD, "members": len(specs), "largest_member": bool(args.batch_largest),
+                   "steps_per_epoch_all_members": sum(sp["steps"] for sp in setup), "nb": 32,
+                   "precision": args.precision, "a_step_of_this_line": "one epoch of every member (one graph replay)",
+                   "branches": batch.n_branches, "kernels_per_epoch": batch.kernels_per_epoch,
+                   "autotuned": bool(args.autotune), "chosen_configs": cfgs,
+                   "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1),
+                   "per_rank": "independent member set, seeds offset by rank (no data-path collective)"},
+        "e2e": {"value": round(ff.item() / t_e2e / 1e9, 2), "unit": UNIT,
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": int(launches) * world,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "epochs_per_s": round(args.steps / t_dev, 3),
+        "wall_s_timed_region": round(wall, 3),
+        "loss_first_last_sum": [sum(loss_first), sum(loss_last)],
+    }
+    # oracle on the host cores: the smallest member, a column sample of one step
+    small = min(specs, key=lambda m: m["nt"] * m["nr"] * m["nv"])
+    w = dict(small)
+    p = synth.make_problem(w["nt"], w["nr"], w["nv"], w["ns"], dx=w["dx"], n_reflectors=w["n_reflectors"],
+                           n_multiples=w["n_multiples"], seed=w["seed"])
+    D64 = p.D.astype(np.float32).astype(np.float64)
+    Uo = np.zeros((w["ns"], w["nv"], w["nt"]))
+    bt = synth.epoch_batches(w["ns"], w["nb"], 1, seed=w["seed"])
+    val, t_step, sample, cores = time_oracle(w, D64, np.zeros((w["nv"], w["nr"], w["nt"])), Uo, bt, target_s=10.0)
+    out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"member nt={w['nt']} nr={w['nr']} nv={w['nv']} ns={w['ns']}: " + sample}
     return out
 
 
@@ -496,7 +680,13 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the plan autotuner choose the FFT radix order and the product kernels")
+    ap.add_argument("--batch-n", type=int, default=48, help=f"{BATCH_WORKLOAD}: number of members")
+    ap.add_argument("--batch-largest", type=int, default=1,
+                    help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")
+    ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"],
                     help="arithmetic of the per-frequency products (the FFTs are FP32 in both)")
     args = ap.parse_args()
@@ -504,6 +694,19 @@ def main():
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == BATCH_WORKLOAD:
+        if args.impl == "reference":
+            ap.error(f"--impl reference times single problems; {BATCH_WORKLOAD} has no reference arm")
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        out = run_gpu_batch(args, rank, world)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     w = workload_dims(args.workload)
     if args.impl == "reference":
         out = run_reference(args, rank, world, w)

@@ -145,6 +145,80 @@ int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx,
 int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float *D, const float *X,
                        const int32_t *idx, int nb, float *U, int *dev_status, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Kernel configuration and autotuning.  Every configuration computes the same operator; they differ
+ * in speed only.  The FFT radix order and the kernel of each per-frequency product are the choices.
+ * A plan made with MDC_PREC_BF16X3 may run the FP32 FMA kernels for a product (they are more
+ * accurate than the split-BF16 bound); the tensor-core kernels are allowed for such plans only.
+ * ------------------------------------------------------------------------------------------- */
+#define MDC_GEMM_SIMT    0   /* FP32 FMA kernels on the CUDA cores (adjoint: tile chosen by size) */
+#define MDC_GEMM_SIMT32  1   /* adjoint only: FP32 FMA, 32 x 32 output tiles */
+#define MDC_GEMM_SIMT64  2   /* adjoint only: FP32 FMA, 64 x 64 output tiles */
+#define MDC_GEMM_TC      3   /* split-BF16 tcgen05 kernels (MDC_PREC_BF16X3 plans only) */
+
+typedef struct {
+    int fft_variant;   /* 0: default radix order of the FFT plan; 1: the reversed order (accepted for
+                          every size, identical to 0 where all radices are equal) */
+    int gemm_fwd;      /* MDC_GEMM_SIMT or MDC_GEMM_TC */
+    int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
+    int reserved[5];   /* zero */
+} mdc_config;
+
+/* The plan's current configuration (host pointer).  New plans start with fft_variant 0 and the
+ * kernels of their precision (SIMT for FP32, TC for BF16X3). */
+int mdc_plan_get_config(mdc_plan_t plan, mdc_config *cfg);
+/* Set the configuration.  MDC_ERR_INVALID_ARG for an unknown value, MDC_ERR_UNSUPPORTED for
+ * MDC_GEMM_TC on an FP32 plan.  Must not be called while work of the plan may still run on the GPU
+ * with the old configuration in a captured graph that is later replayed (a graph keeps the kernels
+ * it captured). */
+int mdc_plan_set_config(mdc_plan_t plan, const mdc_config *cfg);
+/* Autotune: time every candidate of each choice on this plan's sizes, with batch size nb and the
+ * step flags (SMDD_RECIPROCITY changes the adjoint), reps timed launches each after one warm-up, and
+ * keep the fastest.  The FFT candidates are timed on the fused update kernel over a subset of at most
+ * 64 MiB of model traces.  best (host, may be NULL) receives the chosen configuration.
+ * Uses temporary device memory (cudaMalloc), overwrites the plan's spectral workspaces, synchronises
+ * the stream, and must not be called during a stream capture. */
+int mdc_plan_autotune(mdc_plan_t plan, int nb, int flags, int reps, mdc_config *best, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Many independent problems.  The paper solves one MDD problem at a time and has no counterpart;
+ * this serves workloads with many problems of uneven sizes (one per receiver line, frequency band or
+ * survey patch).  A batch holds members, each with its own plan, model, data, source permutations
+ * and step size, and runs whole SGD epochs of every member per call.  mdc_batch_create captures one
+ * epoch of all members into a CUDA graph -- every step of every member, the members spread over
+ * parallel branches (longest first, each onto the least loaded branch) so that small problems share
+ * the GPU -- and mdc_batch_run replays it.  Each step is the smdd_step of the member with
+ * SMDD_KEEP_XHAT, and SMDD_REUSE_XHAT after the first step of the epoch.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct mdc_batch_s *mdc_batch_t;
+
+typedef struct {
+    mdc_plan_t plan;          /* the member's plan: no other batch or call may use it while the batch lives */
+    float *X;                 /* [nv][nr][nt] device, the model, updated in place */
+    const float *U_obs;       /* [ns][nv][nt] device */
+    const int32_t *perm;      /* device int32[n_perm][ns]: epoch e visits the sources in row e % n_perm */
+    int n_perm;               /* >= 1 */
+    int nb;                   /* batch size, 1 .. nb_max of the plan: ceil(ns / nb) steps per epoch, the last partial */
+    float alpha;              /* step size */
+    int flags;                /* 0 or SMDD_RECIPROCITY */
+    double *loss;             /* device float64[loss_rows][ceil(ns/nb)], or NULL: epoch e writes its step
+                                 losses 1/2 ||R||^2 into row e % loss_rows */
+    int loss_rows;            /* >= 1 when loss is given */
+    int reserved[4];          /* zero */
+} smdd_member;
+
+/* Validate the members (host array of n; copied), allocate the per-member epoch buffers and capture
+ * the epoch graph with n_branches parallel branches (1 .. 64; more branches than members is clamped).
+ * stream orders the initialisation; the call returns after it is done.  Nothing runs on the members'
+ * arrays until mdc_batch_run. */
+int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_branches, void *stream);
+/* Run epochs first_epoch .. first_epoch + n_epochs - 1 of every member on stream (asynchronous). */
+int mdc_batch_run(mdc_batch_t batch, long long first_epoch, int n_epochs, void *stream);
+/* Kernel launches in one replay of the epoch graph, and the branch count (host pointers, may be NULL). */
+int mdc_batch_info(mdc_batch_t batch, long long *kernels_per_epoch, int *n_branches);
+/* Release the graph and the batch's buffers (synchronises the device first; the plans stay). */
+int mdc_batch_destroy(mdc_batch_t batch);
+
 /* Wait for all work of this plan's device, then return and clear the device-side status word
  * (MDC_OK, MDC_ERR_INDEX_RANGE, or MDC_ERR_TIMEOUT when a bounded wait of a tensor-core kernel gave up). */
 int mdc_plan_sync_status(mdc_plan_t plan);

@@ -35,10 +35,17 @@ MDC_NUM_STAGES = 7
 MDC_PREC_FP32 = 0
 MDC_PREC_BF16X3 = 1
 
+MDC_GEMM_SIMT = 0
+MDC_GEMM_SIMT32 = 1
+MDC_GEMM_SIMT64 = 2
+MDC_GEMM_TC = 3
+
 EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
+    "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune",
+    "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy",
 )
 
 
@@ -50,6 +57,21 @@ class MDCError(RuntimeError):
 
 class smdd_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class mdc_config(ctypes.Structure):
+    _fields_ = [("fft_variant", ctypes.c_int), ("gemm_fwd", ctypes.c_int), ("gemm_adj", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+    def as_dict(self) -> dict:
+        return {"fft_variant": self.fft_variant, "gemm_fwd": self.gemm_fwd, "gemm_adj": self.gemm_adj}
+
+
+class smdd_member(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("X", ctypes.c_void_p), ("U_obs", ctypes.c_void_p),
+                ("perm", ctypes.c_void_p), ("n_perm", ctypes.c_int), ("nb", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("flags", ctypes.c_int), ("loss", ctypes.c_void_p), ("loss_rows", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -79,6 +101,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_stage_name.argtypes = [i]
     lib.mdc_stage_name.restype = ctypes.c_char_p
     lib.mdc_forward_static.argtypes = [i, i, i, i, f, vp, vp, vp, i, vp, vp, vp]
+    lib.mdc_plan_get_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
+    lib.mdc_plan_set_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
+    lib.mdc_plan_autotune.argtypes = [vp, i, i, i, ctypes.POINTER(mdc_config), vp]
+    lib.mdc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(smdd_member), i, i, vp]
+    lib.mdc_batch_run.argtypes = [vp, ctypes.c_longlong, i, vp]
+    lib.mdc_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
+    lib.mdc_batch_destroy.argtypes = [vp]
     lib.mdc_plan_launch_count.argtypes = [vp]
     lib.mdc_plan_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
@@ -210,6 +239,90 @@ def mdc_forward_static(D: torch.Tensor, X: torch.Tensor, idx: torch.Tensor, U: t
     return U
 
 
+def mdc_plan_get_config(plan: int) -> dict:
+    c = mdc_config()
+    _check(load_library().mdc_plan_get_config(ctypes.c_void_p(plan), ctypes.byref(c)), "mdc_plan_get_config")
+    return c.as_dict()
+
+
+def mdc_plan_set_config(plan: int, fft_variant: int = 0, gemm_fwd: int = MDC_GEMM_SIMT,
+                        gemm_adj: int = MDC_GEMM_SIMT) -> None:
+    c = mdc_config(int(fft_variant), int(gemm_fwd), int(gemm_adj))
+    _check(load_library().mdc_plan_set_config(ctypes.c_void_p(plan), ctypes.byref(c)), "mdc_plan_set_config")
+
+
+def mdc_plan_autotune(plan: int, nb: int, flags: int = 0, reps: int = 5, stream=None) -> dict:
+    c = mdc_config()
+    _check(load_library().mdc_plan_autotune(ctypes.c_void_p(plan), int(nb), int(flags), int(reps), ctypes.byref(c),
+                                            _stream_ptr(stream)), "mdc_plan_autotune")
+    return c.as_dict()
+
+
+class MDCBatch:
+    """Many independent problems, whole SGD epochs replayed from one captured CUDA graph.
+
+    members: list of dicts with keys plan (MDCPlan), X, U_obs, perm (int32 [n_perm][ns]), nb, alpha,
+    flags (0 or SMDD_RECIPROCITY), loss (float64 [loss_rows][steps] or None).  The tensors must stay
+    alive (and at the same addresses) while the batch lives; this object keeps references to them.
+    """
+
+    def __init__(self, members: list, n_branches: int = 8, stream=None):
+        _require_cuda()
+        lib = load_library()
+        arr = (smdd_member * len(members))()
+        self._keep = []
+        self.steps = []
+        for k, m in enumerate(members):
+            plan = m["plan"]
+            X, U, perm = m["X"], m["U_obs"], m["perm"]
+            _dev(X, "X", torch.float32, (plan.nv, plan.nr, plan.nt))
+            _dev(U, "U_obs", torch.float32, (plan.ns, plan.nv, plan.nt))
+            if perm.dim() != 2 or perm.shape[1] != plan.ns:
+                raise ValueError("perm must be [n_perm][ns]")
+            _dev(perm, "perm", torch.int32)
+            nb = int(m["nb"])
+            steps = -(-plan.ns // nb)
+            loss = m.get("loss")
+            if loss is not None:
+                if loss.dim() != 2 or loss.shape[1] != steps:
+                    raise ValueError(f"loss must be [loss_rows][{steps}]")
+                _dev(loss, "loss", torch.float64)
+            arr[k].plan = plan.handle
+            arr[k].X = X.data_ptr()
+            arr[k].U_obs = U.data_ptr()
+            arr[k].perm = perm.data_ptr()
+            arr[k].n_perm = perm.shape[0]
+            arr[k].nb = nb
+            arr[k].alpha = float(m["alpha"])
+            arr[k].flags = int(m.get("flags", 0))
+            arr[k].loss = 0 if loss is None else loss.data_ptr()
+            arr[k].loss_rows = 0 if loss is None else loss.shape[0]
+            self._keep.append((plan, X, U, perm, loss))
+            self.steps.append(steps)
+        h = ctypes.c_void_p()
+        _check(lib.mdc_batch_create(ctypes.byref(h), arr, len(members), int(n_branches), _stream_ptr(stream)),
+               "mdc_batch_create")
+        self.handle = h.value
+        kpe, nbr = ctypes.c_longlong(), ctypes.c_int()
+        _check(lib.mdc_batch_info(ctypes.c_void_p(self.handle), ctypes.byref(kpe), ctypes.byref(nbr)), "mdc_batch_info")
+        self.kernels_per_epoch, self.n_branches = kpe.value, nbr.value
+
+    def run(self, first_epoch: int, n_epochs: int = 1, stream=None) -> None:
+        _check(load_library().mdc_batch_run(ctypes.c_void_p(self.handle), int(first_epoch), int(n_epochs),
+                                            _stream_ptr(stream)), "mdc_batch_run")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load_library().mdc_batch_destroy(ctypes.c_void_p(self.handle)), "mdc_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------------------------------------------
 # convenience object
 # ------------------------------------------------------------------------------------------------
@@ -255,3 +368,14 @@ class MDCPlan:
 
     def sync_status(self) -> int:
         return mdc_plan_sync_status(self.handle)
+
+    def get_config(self) -> dict:
+        return mdc_plan_get_config(self.handle)
+
+    def set_config(self, **cfg) -> None:
+        cur = self.get_config()
+        cur.update(cfg)
+        mdc_plan_set_config(self.handle, **cur)
+
+    def autotune(self, nb: int, flags: int = 0, reps: int = 5) -> dict:
+        return mdc_plan_autotune(self.handle, nb, flags, reps)

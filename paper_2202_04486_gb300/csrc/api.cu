@@ -1,5 +1,6 @@
 // C ABI of the stochastic MDD hot path: plan management, the operator entry points and the SGD step.
 // See include/smdd.h for the contract of every function.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,7 +44,8 @@ struct mdc_plan_s {
     float2 *Dh = nullptr;        // [nf][ns][ldr]
     float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
     float2 *Uh = nullptr;        // [nf][nv][ldb]  batch spectra (prediction, then residual)
-    float2 *tw = nullptr;        // per-pass twiddle tables, tw_size(M) entries
+    float2 *tw = nullptr;        // per-pass twiddle tables of both radix-order variants (variant 1 at tw1_off)
+    int tw1_off = 0;
     float2 *twN = nullptr;       // [M+1]
     double *partials = nullptr;  // residual-kernel block partials
     double *lam = nullptr;       // [nf] power-iteration results, [nf] = max
@@ -57,6 +59,10 @@ struct mdc_plan_s {
     double stage_ms[MDC_NUM_STAGES] = {0};
     long long stage_launches[MDC_NUM_STAGES] = {0};
     long long launches = 0;
+    // kernel configuration (see mdc_config)
+    int fft_variant = 0;
+    int gemm_fwd = MDC_GEMM_SIMT;
+    int gemm_adj = MDC_GEMM_SIMT;
 };
 
 namespace {
@@ -98,7 +104,8 @@ FftArgs base_fft(const mdc_plan_s *p) {
     FftArgs a;
     memset(&a, 0, sizeof(a));
     a.nt = p->nt;
-    a.tw = p->tw;
+    a.tw = p->tw + (p->fft_variant ? p->tw1_off : 0);
+    a.variant = p->fft_variant;
     a.twN = p->twN;
     a.s = p->scale / (float)p->nfft;
     a.status = p->status;
@@ -166,7 +173,7 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.sCf = (long long)p->nv * p->ldb;
     g.outscale = 1.f;
     g.status = p->status;
-    if (p->prec == MDC_PREC_BF16X3)
+    if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
 }
@@ -184,9 +191,10 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.sCf = (long long)p->nv * p->ldr;
     g.outscale = recip ? 0.5f : 1.f;
     g.status = p->status;
-    if (p->prec == MDC_PREC_BF16X3)
+    if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
-    return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st); });
+    const int tile = p->gemm_adj == MDC_GEMM_SIMT32 ? 32 : p->gemm_adj == MDC_GEMM_SIMT64 ? 64 : 0;
+    return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st, tile); });
 }
 
 int check_common(mdc_plan_s *p, const void *a, const void *b, const int32_t *idx, int nb) {
@@ -197,6 +205,29 @@ int check_common(mdc_plan_s *p, const void *a, const void *b, const int32_t *idx
 }
 
 }  // namespace
+
+namespace smdd {
+
+PlanShape plan_shape(const mdc_plan_s *p) {
+    PlanShape sh;
+    sh.nt = p->nt; sh.nr = p->nr; sh.nv = p->nv; sh.ns = p->ns; sh.nbmax = p->nbmax;
+    sh.nfft = p->nfft; sh.nf = p->nf; sh.prec = p->prec; sh.device = p->device;
+    return sh;
+}
+
+bool plan_begin_capture(mdc_plan_s *p) {
+    const bool was = p->profiling;
+    p->profiling = false;   // no timing events inside a graph
+    p->xhat_for = nullptr;
+    return was;
+}
+
+void plan_end_capture(mdc_plan_s *p, bool profiling) {
+    p->profiling = profiling;
+    p->xhat_for = nullptr;  // what the capture recorded has not run
+}
+
+}  // namespace smdd
 
 extern "C" {
 
@@ -247,6 +278,8 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     p->ldb = (nb_max + 1) & ~1;
     p->scale = scale;
     p->prec = precision;
+    p->gemm_fwd = p->gemm_adj = (precision == MDC_PREC_BF16X3) ? MDC_GEMM_TC : MDC_GEMM_SIMT;
+    p->tw1_off = ((fft_tw_size(nfft / 2, 0) > 1 ? fft_tw_size(nfft / 2, 0) : 1) + 1) & ~1;
 
     const int M = p->M, nf = p->nf;
     const size_t szD = (size_t)nf * ns * p->ldr * sizeof(float2);
@@ -257,7 +290,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         p->resid_blocks_max = fft_blocks(M, g);
     }
     bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
-              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)fft_tw_size(M) * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw1_off + fft_tw_size(M, 1) + 1) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->twN, (M + 1) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->partials, (size_t)(p->resid_blocks_max + 1) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&p->lam, (size_t)(nf + 1) * sizeof(double)) == cudaSuccess &&
@@ -270,10 +303,13 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     }
     // per-pass twiddle tables in double precision, rounded once to float
     const double pi = 3.14159265358979323846;
-    std::vector<float2> tw;
-    fft_tw_fill(M, tw);
+    std::vector<float2> tw, tw1;
+    fft_tw_fill(M, tw, 0);
+    fft_tw_fill(M, tw1, 1);
     int rc = MDC_OK;
     if (cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (cudaMemcpyAsync(p->tw + p->tw1_off, tw1.data(), tw1.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = MDC_ERR_CUDA;
     std::vector<float2> twn(M + 1);
     for (int k = 0; k <= M; ++k) {
         const double ang = 2.0 * pi * (double)k / (double)nfft;
@@ -449,6 +485,141 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         if (keep) p->xhat_for = X;
     }
     return MDC_OK;
+}
+
+int mdc_plan_get_config(mdc_plan_t p, mdc_config *cfg) {
+    if (!p || !cfg) return MDC_ERR_INVALID_ARG;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->fft_variant = p->fft_variant;
+    cfg->gemm_fwd = p->gemm_fwd;
+    cfg->gemm_adj = p->gemm_adj;
+    return MDC_OK;
+}
+
+int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
+    if (!p || !cfg) return MDC_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (cfg->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (cfg->fft_variant != 0 && cfg->fft_variant != 1) return MDC_ERR_INVALID_ARG;
+    if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
+    if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
+    if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_adj == MDC_GEMM_TC) && p->prec != MDC_PREC_BF16X3)
+        return MDC_ERR_UNSUPPORTED;
+    // the spectra a plan holds are the same for both radix orders: switching keeps them valid
+    p->fft_variant = fft_has_variant(p->M, cfg->fft_variant) ? cfg->fft_variant : 0;
+    p->gemm_fwd = cfg->gemm_fwd;
+    p->gemm_adj = cfg->gemm_adj;
+    return MDC_OK;
+}
+
+int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *best, void *stream) {
+    if (!p || nb < 1 || reps < 1) return MDC_ERR_INVALID_ARG;
+    if (nb > p->nbmax) return MDC_ERR_SHAPE;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
+    const bool recip = flags & SMDD_RECIPROCITY;
+    if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
+    if (reps > 100) reps = 100;
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return MDC_ERR_INVALID_ARG;
+
+    // scratch: a source list (sources 0, 1, ... cycling through ns) and a subset of model traces
+    const long long trace_bytes = (long long)p->nr * p->nt * (long long)sizeof(float);
+    const int nv_sub = (int)std::max(1LL, std::min((long long)p->nv, (64LL << 20) / std::max(1LL, trace_bytes)));
+    int32_t *didx = nullptr;
+    float *xs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = MDC_OK;
+    std::vector<int32_t> hidx(nb);
+    for (int i = 0; i < nb; ++i) hidx[i] = i % p->ns;
+    if (cudaMalloc(&didx, nb * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&xs, (size_t)nv_sub * trace_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(didx);
+        cudaFree(xs);
+        return MDC_ERR_OOM;
+    }
+    if (cudaMemcpyAsync(didx, hidx.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(xs, 0, (size_t)nv_sub * trace_bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = MDC_ERR_CUDA;
+
+    // mean device time of reps launches of fn after one warm-up launch; < 0 on failure
+    auto time_it = [&](auto &&fn) -> double {
+        if (fn() != MDC_OK) return -1.0;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return -1.0;
+        for (int i = 0; i < reps; ++i)
+            if (fn() != MDC_OK) return -1.0;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+        return (double)ms / reps;
+    };
+    const bool profiling = p->profiling;
+    p->profiling = false;
+    const int old_v = p->fft_variant, old_f = p->gemm_fwd, old_a = p->gemm_adj;
+    int best_v = old_v, best_f = old_f, best_a = old_a;
+    if (rc == MDC_OK) {
+        // FFT radix order, on the fused update (inverse + forward transform of every trace)
+        double tbest = 1e300;
+        for (int v = 0; v < 2 && rc == MDC_OK; ++v) {
+            if (!fft_has_variant(p->M, v)) continue;
+            p->fft_variant = v;
+            const double t = time_it([&] {
+                FftArgs a = base_fft(p);
+                a.g = model_grid(p, nv_sub);
+                a.tout = xs;
+                a.vec = vec4_ok(p->nt, xs);
+                a.spec = p->Xh;
+                a.alpha = 0.f;
+                return launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, true, a, st); });
+            });
+            if (t < 0) rc = MDC_ERR_CUDA;
+            else if (t < tbest) { tbest = t; best_v = v; }
+        }
+        p->fft_variant = best_v;
+    }
+    if (rc == MDC_OK) {
+        double tbest = 1e300;
+        const int cand[2] = {MDC_GEMM_SIMT, MDC_GEMM_TC};
+        for (int c : cand) {
+            if (c == MDC_GEMM_TC && p->prec != MDC_PREC_BF16X3) continue;
+            p->gemm_fwd = c;
+            const double t = time_it([&] { return gemm_forward(p, didx, nb, st); });
+            if (t < 0) { rc = MDC_ERR_CUDA; break; }
+            if (t < tbest) { tbest = t; best_f = c; }
+        }
+    }
+    if (rc == MDC_OK) {
+        double tbest = 1e300;
+        const int cand[3] = {MDC_GEMM_SIMT32, MDC_GEMM_SIMT64, MDC_GEMM_TC};
+        for (int c : cand) {
+            if (c == MDC_GEMM_TC && p->prec != MDC_PREC_BF16X3) continue;
+            p->gemm_adj = c;
+            const double t = time_it([&] { return gemm_adjoint(p, didx, nb, recip, st); });
+            if (t < 0) { rc = MDC_ERR_CUDA; break; }
+            if (t < tbest) { tbest = t; best_a = c; }
+        }
+    }
+    p->profiling = profiling;
+    p->xhat_for = nullptr;   // the spectral workspaces were overwritten
+    if (rc == MDC_OK) {
+        p->fft_variant = best_v;
+        p->gemm_fwd = best_f;
+        p->gemm_adj = best_a;
+    } else {
+        p->fft_variant = old_v;
+        p->gemm_fwd = old_f;
+        p->gemm_adj = old_a;
+    }
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(didx);
+    cudaFree(xs);
+    if (rc == MDC_OK && best) mdc_plan_get_config(p, best);
+    return rc;
 }
 
 int mdc_plan_sync_status(mdc_plan_t p) {

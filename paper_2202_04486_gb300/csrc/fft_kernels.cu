@@ -15,6 +15,8 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
 #include "smdd_fft.cuh"
 #include "smdd_internal.h"
 
@@ -88,10 +90,10 @@ __device__ __forceinline__ void tile_store_spec(const float2 *sm, float2 *__rest
 // hold samples (the upper half is the zero padding since nt <= M).  Slot h = qq * (R_1/2) + r.
 constexpr int NPAIR = FFT_P / 4;   // float4 slots per thread
 
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void load_pairs(const float *__restrict__ x, int nt, bool valid, bool vec, int t,
                                            float4 (&h)[NPAIR]) {
-    constexpr int R = fft_radix(M, 0), T = M / FFT_P, QQ = FFT_P / R / 2, S = M / R;
+    constexpr int R = fft_radix(M, 0, V), T = M / FFT_P, QQ = FFT_P / R / 2, S = M / R;
 #pragma unroll
     for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
@@ -113,9 +115,9 @@ __device__ __forceinline__ void load_pairs(const float *__restrict__ x, int nt, 
 }
 
 // pairs -> first-forward-pass registers (upper half of every butterfly is zero padding)
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void pairs_to_regs(const float4 (&h)[NPAIR], float2 (&a)[FFT_P]) {
-    constexpr int R = fft_radix(M, 0), QQ = FFT_P / R / 2;
+    constexpr int R = fft_radix(M, 0, V), QQ = FFT_P / R / 2;
 #pragma unroll
     for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
@@ -141,7 +143,7 @@ __device__ __forceinline__ void store_quad(float *y, int i0, int nt, bool vec, f
 // ------------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------------
-template <int M>
+template <int M, int V>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T;
@@ -151,25 +153,25 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArg
     float4 h[NPAIR];
     float2 v[FFT_P];
     const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    load_pairs<M>(x, a.nt, c.valid, a.vec, t, h);
-    pairs_to_regs<M>(h, v);
-    rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, h);
+    pairs_to_regs<M, V>(h, v);
+    rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
 }
 
 // spectra -> s * irfft, causal window [0, nt)
-template <int M>
+template <int M, int V>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_irfft_out(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     const TileCoord c = coord_of<M>(a.g, tr);
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
-    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
     if (!c.valid) return;   // no barrier follows
     float *y = a.tout + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj;
 #pragma unroll
@@ -207,12 +209,12 @@ __device__ __forceinline__ float4 resid_quad(float2 p0, float2 p1, float4 o, flo
 
 // Residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], loss partial 1/2 sum R^2 (FP64), Rh = rfft(R)
 // written in place over Uh.  Trace grid: i = batch entry b, j = virtual source v.
-template <int M>
+template <int M, int V>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[32];
     __shared__ bool am_last;
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord c = coord_of<M>(a.g, tr);
 
@@ -230,13 +232,13 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
         if (row >= 0) uo = a.uobs + (long long)row * a.uo_si + (long long)c.j * a.uo_sj;
     }
     float4 o[NPAIR];
-    load_pairs<M>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o);
+    load_pairs<M, V>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o);
 
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
-    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
 
     double l2 = 0.0;
     float4 z[NPAIR];
@@ -253,9 +255,9 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
             }
             z[hs] = q;
         }
-    pairs_to_regs<M>(z, v);
+    pairs_to_regs<M, V>(z, v);
     team_sync<T>();          // every thread of the team has finished reading buf
-    rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile_store_spec<M>(sm, a.spec, a.g);
 
@@ -283,21 +285,21 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
 
 // SGD update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g;  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
-template <int M, bool KEEP>
+template <int M, int V, bool KEEP>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
-    constexpr int T = Team<M>::T, R = fft_radix(M, 0), QQ = FFT_P / R / 2, S = M / R;
+    constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord c = coord_of<M>(a.g, tr);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     float4 xo[NPAIR];
-    load_pairs<M>(x, a.nt, c.valid, a.vec, t, xo);      // model samples, prefetched
+    load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo);      // model samples, prefetched
 
     tile_load_spec<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
-    irfft_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
     const float nas = -a.alpha * a.s;
 #pragma unroll
     for (int qq = 0; qq < QQ; ++qq)
@@ -316,9 +318,9 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
             xo[hs] = z;
         }
     if constexpr (KEEP) {
-        pairs_to_regs<M>(xo, v);
+        pairs_to_regs<M, V>(xo, v);
         team_sync<T>();
-        rfft_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+        rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
         __syncthreads();
         tile_store_spec<M>(sm, a.spec, a.g);
     }
@@ -374,26 +376,28 @@ int fft_blocks(int M, const TraceGrid &g) {
     return 0;
 }
 
-int fft_tw_size(int M) {
+int fft_tw_size(int M, int v) {
     switch (M) {
-        case 32: return tw_size(32);
-        case 64: return tw_size(64);
-        case 128: return tw_size(128);
-        case 256: return tw_size(256);
-        case 512: return tw_size(512);
-        case 1024: return tw_size(1024);
-        case 2048: return tw_size(2048);
-        case 4096: return tw_size(4096);
+        case 32: return tw_size(32, v);
+        case 64: return tw_size(64, v);
+        case 128: return tw_size(128, v);
+        case 256: return tw_size(256, v);
+        case 512: return tw_size(512, v);
+        case 1024: return tw_size(1024, v);
+        case 2048: return tw_size(2048, v);
+        case 4096: return tw_size(4096, v);
     }
     return 0;
 }
 
-void fft_tw_fill(int M, std::vector<float2> &tw) {
+bool fft_has_variant(int M, int v) { return v == 0 || (v == 1 && fft_variant_distinct(M)); }
+
+void fft_tw_fill(int M, std::vector<float2> &tw, int v) {
     const double pi = 3.14159265358979323846;
-    tw.assign(fft_tw_size(M) > 0 ? fft_tw_size(M) : 1, make_float2(0.f, 0.f));
+    tw.assign(fft_tw_size(M, v) > 0 ? fft_tw_size(M, v) : 1, make_float2(0.f, 0.f));
     for (int inv = 0; inv < 2; ++inv)
         for (int p = 1; p < fft_npass(M); ++p) {
-            const int NS = dir_span(M, inv, p), R = dir_radix(M, inv, p), off = tw_off(M, inv, p);
+            const int NS = dir_span(M, inv, p, v), R = dir_radix(M, inv, p, v), off = tw_off(M, inv, p, v);
             for (int k = 0; k < NS; ++k)
                 for (int r = 0; r < R; ++r) {
                     const double ang = 2.0 * pi * (double)(r * k) / (double)(NS * R);
@@ -402,16 +406,35 @@ void fft_tw_fill(int M, std::vector<float2> &tw) {
         }
 }
 
+// call f(std::integral_constant<int, V>) with V the radix-order variant (variant 1 only where it differs)
+template <int M, class F>
+static void with_variant(int v, F &&f) {
+    if constexpr (fft_variant_distinct(M)) {
+        if (v == 1) f(std::integral_constant<int, 1>{});
+        else f(std::integral_constant<int, 0>{});
+    } else {
+        f(std::integral_constant<int, 0>{});
+    }
+}
+
+template <int M>
+static cudaError_t prepare_m() {
+    const int sm = (int)Team<M>::SMEM;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 2; ++v)
+        with_variant<M>(v, [&](auto vc) {
+            constexpr int V = decltype(vc)::value;
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rfft<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_irfft_out<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residual<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        });
+    return e;
+}
+
 cudaError_t fft_prepare(int M) {
-    SMDD_SWITCH_M(M, {
-        const int sm = (int)Team<MM>::SMEM;
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_rfft<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-        if ((e = cudaFuncSetAttribute(k_irfft_out<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-        if ((e = cudaFuncSetAttribute(k_residual<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-        if ((e = cudaFuncSetAttribute(k_update<MM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-        if ((e = cudaFuncSetAttribute(k_update<MM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    });
+    SMDD_SWITCH_M(M, { return prepare_m<MM>(); });
     return cudaSuccess;
 }
 
@@ -419,7 +442,9 @@ cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
-        k_rfft<MM><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        with_variant<MM>(a.variant, [&](auto vc) {
+            k_rfft<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        });
     });
     return cudaGetLastError();
 }
@@ -428,7 +453,9 @@ cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
-        k_irfft_out<MM><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        with_variant<MM>(a.variant, [&](auto vc) {
+            k_irfft_out<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        });
     });
     return cudaGetLastError();
 }
@@ -437,7 +464,9 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
-        k_residual<MM><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        with_variant<MM>(a.variant, [&](auto vc) {
+            k_residual<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        });
     });
     return cudaGetLastError();
 }
@@ -446,8 +475,11 @@ cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
-        if (keep) k_update<MM, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
-        else k_update<MM, false><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        with_variant<MM>(a.variant, [&](auto vc) {
+            constexpr int V = decltype(vc)::value;
+            if (keep) k_update<MM, V, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+            else k_update<MM, V, false><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        });
     });
     return cudaGetLastError();
 }

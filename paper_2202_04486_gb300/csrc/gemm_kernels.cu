@@ -390,10 +390,12 @@ static void launch_adj_tt(const GemmArgs &a0, bool recip, int nf, cudaStream_t s
     }
 }
 
-cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st) {
+cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, int tile) {
     // 32-wide tiles waste less of the (triangular, ragged) output at moderate sizes; 64-wide tiles
-    // re-use each staged operand for twice the products when the matrices are large
-    if (a.nv <= 512 && a.nr <= 512) launch_adj_tt<32>(a, recip, nf, st);
+    // re-use each staged operand for twice the products when the matrices are large (tile = 0: choose
+    // by that rule; 32 or 64: as given)
+    if (tile == 0) tile = (a.nv <= 512 && a.nr <= 512) ? 32 : 64;
+    if (tile == 32) launch_adj_tt<32>(a, recip, nf, st);
     else launch_adj_tt<64>(a, recip, nf, st);
     return cudaGetLastError();
 }

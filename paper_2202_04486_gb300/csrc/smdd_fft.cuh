@@ -107,7 +107,10 @@ __device__ __forceinline__ void dftR(float2 *a) {
 constexpr int FFT_P = 16;   // complex values per thread
 
 __host__ __device__ constexpr int fft_npass(int M) { return M <= 64 ? 2 : M <= 512 ? 3 : 4; }
-__host__ __device__ constexpr int fft_radix(int M, int p) {
+// variant 0: the default radix order; variant 1: the same radices in reverse order (identical to
+// variant 0 where every radix is 8).  Both are valid Stockham plans; which one is faster for a given
+// shape is left to measurement (the plan autotuner).
+__host__ __device__ constexpr int fft_radix0(int M, int p) {
     return M == 32 ? (p == 0 ? 8 : 4)
          : M == 64 ? 8
          : M == 128 ? (p == 0 ? 8 : 4)
@@ -117,27 +120,35 @@ __host__ __device__ constexpr int fft_radix(int M, int p) {
          : M == 2048 ? (p == 3 ? 4 : 8)
          : 8;  // 4096
 }
-__host__ __device__ constexpr int fft_span(int M, int p) {
-    return p == 0 ? 1 : fft_span(M, p - 1) * fft_radix(M, p - 1);
+__host__ __device__ constexpr int fft_radix(int M, int p, int v = 0) {
+    return v == 0 ? fft_radix0(M, p) : fft_radix0(M, fft_npass(M) - 1 - p);
 }
-__host__ __device__ constexpr int ifft_radix(int M, int p) { return fft_radix(M, fft_npass(M) - 1 - p); }
-__host__ __device__ constexpr int ifft_span(int M, int p) {
-    return p == 0 ? 1 : ifft_span(M, p - 1) * ifft_radix(M, p - 1);
+__host__ __device__ constexpr bool fft_variant_distinct(int M) {
+    for (int p = 0; p < fft_npass(M); ++p)
+        if (fft_radix(M, p, 0) != fft_radix(M, p, 1)) return true;
+    return false;
 }
-__host__ __device__ constexpr int dir_radix(int M, bool inv, int p) { return inv ? ifft_radix(M, p) : fft_radix(M, p); }
-__host__ __device__ constexpr int dir_span(int M, bool inv, int p) { return inv ? ifft_span(M, p) : fft_span(M, p); }
+__host__ __device__ constexpr int fft_span(int M, int p, int v = 0) {
+    return p == 0 ? 1 : fft_span(M, p - 1, v) * fft_radix(M, p - 1, v);
+}
+__host__ __device__ constexpr int ifft_radix(int M, int p, int v = 0) { return fft_radix(M, fft_npass(M) - 1 - p, v); }
+__host__ __device__ constexpr int ifft_span(int M, int p, int v = 0) {
+    return p == 0 ? 1 : ifft_span(M, p - 1, v) * ifft_radix(M, p - 1, v);
+}
+__host__ __device__ constexpr int dir_radix(int M, bool inv, int p, int v = 0) { return inv ? ifft_radix(M, p, v) : fft_radix(M, p, v); }
+__host__ __device__ constexpr int dir_span(int M, bool inv, int p, int v = 0) { return inv ? ifft_span(M, p, v) : fft_span(M, p, v); }
 
 // Twiddle tables, one per pass p >= 1 of each direction: entry [r][k] (r < R, k < Ns) holds
 // w_{Ns R}^{r k} (forward roots; the inverse multiplies by their conjugates).  k is the fast index, so
 // the adjacent butterflies of a thread and of neighbouring lanes read adjacent entries.  Offsets in float2.
-__host__ __device__ constexpr int tw_off(int M, bool inv, int p) {
+__host__ __device__ constexpr int tw_off(int M, bool inv, int p, int v = 0) {
     int off = 0;
     if (inv)
-        for (int q = 1; q < fft_npass(M); ++q) off += fft_span(M, q) * fft_radix(M, q);
-    for (int q = 1; q < p; ++q) off += dir_span(M, inv, q) * dir_radix(M, inv, q);
+        for (int q = 1; q < fft_npass(M); ++q) off += fft_span(M, q, v) * fft_radix(M, q, v);
+    for (int q = 1; q < p; ++q) off += dir_span(M, inv, q, v) * dir_radix(M, inv, q, v);
     return off;
 }
-__host__ __device__ constexpr int tw_size(int M) { return tw_off(M, true, fft_npass(M)); }
+__host__ __device__ constexpr int tw_size(int M, int v = 0) { return tw_off(M, true, fft_npass(M), v); }
 
 // Shared-memory layout of one trace: element i at float2 index i + 2 (i / 16).  The padding keeps
 // every pair (2m, 2m+1) 16-byte aligned and makes the 128-bit accesses of the passes bank-conflict
@@ -272,20 +283,20 @@ __device__ __forceinline__ void pass_store(float2 *buf, int t, const float2 (&a)
     }
 }
 
-template <int M, bool INV, int p, int PEND>
+template <int M, bool INV, int p, int PEND, int V>
 __device__ __forceinline__ void passes_from(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw) {
     // passes p .. PEND-1 of a direction: load, compute, and (except for the last inverse pass) store
     if constexpr (p < PEND) {
-        constexpr int R = dir_radix(M, INV, p), NS = dir_span(M, INV, p);
+        constexpr int R = dir_radix(M, INV, p, V), NS = dir_span(M, INV, p, V);
         pass_load<M, R>(buf, t, a);
         if constexpr (!INV) team_sync<M / FFT_P>();
-        pass_compute<M, R, NS, INV, tw_off(M, INV, p)>(a, t, tw);
+        pass_compute<M, R, NS, INV, tw_off(M, INV, p, V)>(a, t, tw);
         if constexpr (!INV || p + 1 < fft_npass(M)) {
             if constexpr (INV) team_sync<M / FFT_P>();
             pass_store<M, R, NS>(buf, t, a);
             team_sync<M / FFT_P>();
         }
-        passes_from<M, INV, p + 1, PEND>(a, buf, t, tw);
+        passes_from<M, INV, p + 1, PEND, V>(a, buf, t, tw);
     }
 }
 
@@ -311,20 +322,20 @@ __device__ __forceinline__ float2 root32(int m) {
 // owns the pairs u = t + T q (q < 8/R) and, for each, the butterflies ja = u and jb = M/R - u
 // (jb = M/(2R) for u = 0).  The bins k = ja + r M/R and M - k = jb + (R-1-r) M/R then lie in the same
 // thread, so the real-signal post- and pre-processing run in registers.
-template <int M>
+template <int M, int V>
 struct EdgePass {
-    static constexpr int R = fft_radix(M, fft_npass(M) - 1);
+    static constexpr int R = fft_radix(M, fft_npass(M) - 1, V);
     static constexpr int S = M / R;     // span of the last forward pass = stride of its inputs
     static constexpr int NP = 8 / R;    // pairs per thread
 };
 
 // Last forward pass + real post-processing.  Input: buf after the other forward passes.  Output: buf
 // holds X[1..M-1] in their slots and (X[0], X[M]) in slot 0.  Ends with a team sync.
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void fwd_last_real(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
                                               const float2 *__restrict__ twN) {
-    constexpr int T = M / FFT_P, R = EdgePass<M>::R, S = EdgePass<M>::S, NP = EdgePass<M>::NP;
-    constexpr int TWOFF = tw_off(M, false, fft_npass(M) - 1);
+    constexpr int T = M / FFT_P, R = EdgePass<M, V>::R, S = EdgePass<M, V>::S, NP = EdgePass<M, V>::NP;
+    constexpr int TWOFF = tw_off(M, false, fft_npass(M) - 1, V);
     int ja[NP], jb[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -384,9 +395,9 @@ __device__ __forceinline__ void fwd_last_real(float2 (&a)[FFT_P], float2 *buf, i
 // First inverse pass with the real pre-processing: buf holds a real-signal spectrum (slot 0 = (X[0],
 // X[M])).  Forms Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) w_N^{-k}, applies the
 // radix-R inverse butterflies and stores the pass output.  Ends with a team sync.
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void inv_first_real(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ twN) {
-    constexpr int T = M / FFT_P, R = EdgePass<M>::R, S = EdgePass<M>::S, NP = EdgePass<M>::NP;
+    constexpr int T = M / FFT_P, R = EdgePass<M, V>::R, S = EdgePass<M, V>::S, NP = EdgePass<M, V>::NP;
     int ja[NP], jb[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -439,25 +450,25 @@ __device__ __forceinline__ void inv_first_real(float2 (&a)[FFT_P], float2 *buf, 
 // Forward real FFT of length 2M.  Input: registers in first-pass order (time samples).  Output: the
 // real-signal spectrum in buf (slot 0 = (X[0], X[M]), bins 1..M-1 in their slots, padded layout).  Ends
 // with a team sync.  No thread of the team may still read buf on entry.
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void rfft_regs_to_smem(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
                                                   const float2 *__restrict__ twN) {
-    constexpr int R0 = fft_radix(M, 0);
+    constexpr int R0 = fft_radix(M, 0, V);
     pass_compute<M, R0, 1, false, 0>(a, t, tw);
     pass_store<M, R0, 1>(buf, t, a);
     team_sync<M / FFT_P>();
-    passes_from<M, false, 1, fft_npass(M) - 1>(a, buf, t, tw);
-    fwd_last_real<M>(a, buf, t, tw, twN);
+    passes_from<M, false, 1, fft_npass(M) - 1, V>(a, buf, t, tw);
+    fwd_last_real<M, V>(a, buf, t, tw, twN);
 }
 
 // Inverse real FFT of length 2M (unnormalised: yields 2M x).  Input: real-signal spectrum in buf.
 // Output: registers in first-forward-pass order (time samples).  The last pass reads buf, so the caller
 // must sync the team before writing buf again.
-template <int M>
+template <int M, int V>
 __device__ __forceinline__ void irfft_smem_to_regs(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
                                                    const float2 *__restrict__ twN) {
-    inv_first_real<M>(a, buf, t, twN);
-    passes_from<M, true, 1, fft_npass(M)>(a, buf, t, tw);
+    inv_first_real<M, V>(a, buf, t, twN);
+    passes_from<M, true, 1, fft_npass(M), V>(a, buf, t, tw);
 }
 
 }  // namespace smdd

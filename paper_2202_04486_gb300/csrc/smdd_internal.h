@@ -42,6 +42,7 @@ struct FftArgs {
     unsigned int *counter;
     double *loss;
     int *status;
+    int variant;             // radix-order variant of the FFT plan (0 or 1, see fft_radix)
 };
 
 struct GemmArgs {
@@ -63,18 +64,27 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
 cudaError_t launch_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
 int fft_blocks(int M, const TraceGrid &g);
 int fft_traces_per_cta(int M);
-cudaError_t fft_prepare(int M);
-int fft_tw_size(int M);
-void fft_tw_fill(int M, std::vector<float2> &tw);   // host: per-pass twiddle tables   // opt-in to the dynamic shared memory the kernels of size M need
+cudaError_t fft_prepare(int M);                                // opt-in to the dynamic shared memory of size M
+int fft_tw_size(int M, int variant = 0);
+bool fft_has_variant(int M, int variant);                     // variant 1 exists where it differs from 0
+void fft_tw_fill(int M, std::vector<float2> &tw, int variant = 0);   // host: per-pass twiddle tables
 
 cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
-cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
+cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, int tile = 0);
 cudaError_t gemm_prepare();
 
 // split-BF16 tensor-core products (tcgen05)
 cudaError_t tc_prepare();
 cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
+
+// plan internals used by the batch runner (api.cu)
+struct PlanShape {
+    int nt, nr, nv, ns, nbmax, nfft, nf, prec, device;
+};
+PlanShape plan_shape(const mdc_plan_s *p);
+bool plan_begin_capture(mdc_plan_s *p);               // returns the profiling flag it switched off
+void plan_end_capture(mdc_plan_s *p, bool profiling);
 
 cudaError_t launch_power_iter(const float2 *Dh, int ns, int nr, int ldr, long long sDf, int nf, int n_iter,
                               double *lam, cudaStream_t st);

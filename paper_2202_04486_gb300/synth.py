@@ -85,6 +85,71 @@ def make_problem(nt: int, nr: int, nv: int, ns: int, *, dx: float = 20.0, dt: fl
     return Problem(nt, nr, nv, ns, dt, dx, D, X, noise)
 
 
+def make_problem_device(nt: int, nr: int, nv: int, ns: int, *, dx: float = 20.0, dt: float = DT,
+                        n_reflectors: int = 3, n_multiples: int = 2, seed: int = 0, device=None,
+                        chunk: int = 64):
+    """make_problem for sizes too large for host-side float64 generation: the same formulas and the
+    same random draws (the reflector parameters come from the same numpy generator, in the same
+    order), evaluated with torch in float64 on `device`, chunk sources / virtual sources at a time,
+    and returned as float32 tensors (D, X_true).  No noise is drawn."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    vel = rng.uniform(1500.0, 2500.0, n_reflectors)
+    amp = rng.uniform(0.2, 1.0, n_reflectors)
+    t0 = rng.uniform(0.15, 0.85, n_reflectors) * nt * dt
+    f64 = dict(device=device, dtype=torch.float64)
+    t = torch.arange(nt, **f64) * dt
+    xr = torch.arange(nr, **f64) * dx
+
+    def ricker_t(x):
+        a = (math.pi * F0 * x) ** 2
+        return (1.0 - 2.0 * a) * torch.exp(-a)
+
+    X = torch.empty((nv, nr, nt), device=device, dtype=torch.float32)
+    for v0 in range(0, nv, chunk):
+        xv = torch.arange(v0, min(nv, v0 + chunk), **f64) * dx
+        off = xr[None, :] - xv[:, None]
+        acc = torch.zeros((xv.numel(), nr, nt), **f64)
+        for k in range(n_reflectors):
+            tk = torch.sqrt(t0[k] ** 2 + (off / vel[k]) ** 2)
+            acc += amp[k] * ricker_t(t[None, None, :] - tk[:, :, None])
+        X[v0:v0 + xv.numel()] = acc.float()
+    delta = 0.2 * nt * dt
+    D = torch.empty((ns, nr, nt), device=device, dtype=torch.float32)
+    for s0 in range(0, ns, chunk):
+        xs = torch.arange(s0, min(ns, s0 + chunk), **f64) * dx
+        off = xs[:, None] - xr[None, :]
+        acc = torch.zeros((xs.numel(), nr, nt), **f64)
+        for m in range(n_multiples + 1):
+            tm = torch.sqrt((T_DIRECT + m * delta) ** 2 + (off / WATER_V) ** 2)
+            acc += (-0.5) ** m * ricker_t(t[None, None, :] - tm[:, :, None])
+        D[s0:s0 + xs.numel()] = acc.float()
+    return D, X
+
+
+def batch_members(n: int = 48, *, seed: int = 1000, nb: int = 32, largest=(1500, 1200, 1200, 1200)) -> list[dict]:
+    """Shapes of a set of independent MDD problems of uneven sizes: n - 1 members with
+    nr, nv ~ U[64, 600], ns ~ U[64, 800], nt in {256, 512, 1024, 1500} (member i drawn from seed + i and
+    generated with that seed), plus one fixed largest member (nt, nr, nv, ns) = largest (None: none).
+    Every member: batch nb, 20 m spacing, 8 reflectors, 4 multiple orders, no noise, reciprocity only
+    where nr == nv."""
+    out = []
+    for i in range(n - (1 if largest else 0)):
+        r = np.random.default_rng(seed + i)
+        nt = int(r.choice([256, 512, 1024, 1500]))
+        nr = int(r.integers(64, 601))
+        nv = int(r.integers(64, 601))
+        ns = int(r.integers(64, 801))
+        out.append(dict(nt=nt, nr=nr, nv=nv, ns=ns, nb=nb, seed=seed + i))
+    if largest:
+        nt, nr, nv, ns = largest
+        out.append(dict(nt=nt, nr=nr, nv=nv, ns=ns, nb=nb, seed=seed + n - 1))
+    for m in out:
+        m.update(dx=20.0, n_reflectors=8, n_multiples=4, reciprocity=m["nr"] == m["nv"])
+    return out
+
+
 def epoch_batches(ns: int, nb: int, n_epochs: int, seed: int = 0) -> list[list[np.ndarray]]:
     """Source batches for n_epochs of stochastic MDD.
 
