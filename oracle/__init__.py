@@ -16,7 +16,9 @@ too slow (multi-epoch trajectories).
 Pins (tests/test_oracle_pins.py): the 1D case against numpy.convolve / numpy.correlate, a delta
 down-going field, a dense operator built from scipy Toeplitz blocks, the adjoint dot-product test, the
 finite-sum identity of Eq. 5/6, the Landweber toy of Eq. 11 (sigma^2 = 53.0256), the spectral bound on
-the operator norm, and SGD converging to the least-squares solution of a tiny consistent problem.
+the operator norm, SGD converging to the least-squares solution of a tiny consistent problem, and for
+N-SGD: the equivalence of the look-ahead form with Sutskever's form, mu = 0 giving SGD, and convergence
+to the minimum-norm least-squares solution; the causality mute against an explicit loop.
 
 Readings of the paper taken here (each is also listed in the design notes):
   * scale: the receiver integral of Eq. 1 is a plain sum over receivers times `scale` (default 1).
@@ -25,6 +27,9 @@ Readings of the paper taken here (each is also listed in the design notes):
   * reciprocity preconditioner C_r: 1/2 (G + G^T) with T swapping receiver and virtual source.
   * steps per epoch: ceil(ns / nb), the last batch partial.
   * RMSE (Eq. 7): plain L2 norm of the difference of the max-normalised fields.
+  * N-SGD: Nesterov momentum in Sutskever's form, evaluated on the look-ahead point (nsgd_step).
+  * causality preconditioner C_c: a per-trace first kept sample (the direct-arrival mute); with
+    reciprocity the mute table is symmetric in (r, v).
 """
 from __future__ import annotations
 
@@ -196,6 +201,44 @@ def run_epochs(D, X0, U_obs, batches, alpha: float, *, recip: bool = False, scal
             X, l = sgd_step(D, X, U_obs, idx, alpha, recip=recip, scale=scale, fft=fft)
             losses.append(l)
     return X, losses
+
+
+def causal_mute(G, first):
+    """Causality preconditioner C_c (Eq. 4; the space-time mask of the Volve examples that mutes the
+    reflection response above the direct arrival): samples t < first[v, r] of trace (v, r) set to zero.
+    first: int array [nv, nr].  C_c is diagonal with 0/1 entries, so it is its own adjoint."""
+    G = _f64(G).copy()
+    first = np.asarray(first)
+    t = np.arange(G.shape[-1])
+    G[t[None, None, :] < first[:, :, None]] = 0.0
+    return G
+
+
+def precondition(g, *, recip: bool = False, mute=None):
+    """C^T g for the chain C = C_r C_c of Eq. 4 (reciprocity and causality, either optional).  With a
+    mute table symmetric in (r, v) the two commute and C_r C_c C_c^T C_r^T g = C_c C_r g: the model stays
+    in the range of C when it starts there."""
+    if recip:
+        g = reciprocity(g)
+    if mute is not None:
+        g = causal_mute(g, mute)
+    return g
+
+
+def nsgd_step(D, X, V, U_obs, idx, alpha: float, mu: float, *, recip: bool = False, mute=None,
+              scale: float = 1.0, fft: bool = False):
+    """One step of SGD with Nesterov momentum (the N-SGD solver; momentum after Sutskever et al. 2013),
+    written on the look-ahead point.  Sutskever's form is
+        v' = mu v - alpha grad f(x + mu v),   x' = x + v';
+    with y = x + mu v (the point where the gradient is taken) it becomes
+        v' = mu v - alpha grad f(y),          y' = y + mu v' - alpha grad f(y),
+    and X here is y.  grad f is the preconditioned mini-batch gradient C^T g_B of Eq. 6.
+    Returns (X_new, V_new, loss)."""
+    g, l, _ = gradient(D, X, U_obs, idx, scale, fft)
+    g = precondition(g, recip=recip, mute=mute)
+    V_new = mu * _f64(V) - alpha * g
+    X_new = _f64(X) + mu * V_new - alpha * g
+    return X_new, V_new, l
 
 
 def steps_per_epoch(ns: int, nb: int) -> int:

@@ -150,6 +150,17 @@ def batch_members(n: int = 48, *, seed: int = 1000, nb: int = 32, largest=(1500,
     return out
 
 
+def direct_arrival_mute(nr: int, nv: int, nt: int, *, dx: float = 20.0, dt: float = DT,
+                        v_max: float = 2500.0, lead: float = 1.5 / F0) -> np.ndarray:
+    """First kept sample of each reflection-response trace for the causality mute: the earliest
+    hyperbola of the generator at offset h = |x_r - x_v| cannot arrive before h / v_max, and a Ricker
+    wavelet starts about `lead` before its peak, so samples before (h / v_max - lead) / dt hold no
+    signal.  Returns int32 [nv, nr]; symmetric in (r, v) on the shared positions."""
+    h = np.abs(np.arange(nr)[None, :] - np.arange(nv)[:, None]) * dx
+    first = np.floor((h / v_max - lead) / dt)
+    return np.clip(first, 0, nt).astype(np.int32)
+
+
 def epoch_batches(ns: int, nb: int, n_epochs: int, seed: int = 0) -> list[list[np.ndarray]]:
     """Source batches for n_epochs of stochastic MDD.
 

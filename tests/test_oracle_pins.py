@@ -291,3 +291,97 @@ def test_generator_reciprocal_and_seeded():
     q = synth.make_problem(64, 6, 6, 7, seed=3)
     np.testing.assert_array_equal(p.D, q.D)
     assert np.max(np.abs(p.D)) > 0.5 and np.max(np.abs(p.X_true)) > 0.1
+
+
+# ------------------------------------------------------------------------------------------------
+# N-SGD (Nesterov momentum after Sutskever et al. 2013) and the causality mute
+# ------------------------------------------------------------------------------------------------
+def _dense_quadratic(seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((12, 7)) @ np.diag([3, 2, 1.5, 1, 0.7, 0.5, 0.3])
+    b = rng.standard_normal(12)
+    return A, b
+
+
+def test_nsgd_lookahead_form_equals_sutskever_form():
+    """With nt = 1 and one virtual source the MDC is a dense product, U[s] = sum_r D[s, r] x[r], so the
+    oracle's N-SGD steps on f(x) = 1/2 ||A x - b||^2 (A = D[:, :, 0]) can be checked against Sutskever's
+    form iterated directly: gradient at x + mu v, x' = x + v'; the oracle's X is y = x + mu v."""
+    A, b = _dense_quadratic(5)
+    alpha, mu = 0.02, 0.9
+    D = A[:, :, None]
+    U = b[:, None, None]
+    grad = lambda z: A.T @ (A @ z - b)
+    x, v = np.zeros(7), np.zeros(7)
+    Y, W = np.zeros((1, 7, 1)), np.zeros((1, 7, 1))
+    for _ in range(40):
+        v = mu * v - alpha * grad(x + mu * v)
+        x = x + v
+        Y, W, _ = oracle.nsgd_step(D, Y, W, U, np.arange(12), alpha, mu)
+        np.testing.assert_allclose(Y.ravel(), x + mu * v, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(W.ravel(), v, rtol=1e-11, atol=1e-12)
+
+
+def test_nsgd_with_zero_momentum_is_sgd():
+    nt, nr, nv, ns = 20, 4, 3, 6
+    D = synth.random_traces((ns, nr, nt), 1)
+    X = synth.random_traces((nv, nr, nt), 2)
+    U = synth.random_traces((ns, nv, nt), 3)
+    idx = np.array([4, 1, 2])
+    Xs, ls = oracle.sgd_step(D, X, U, idx, 0.01)
+    g, _, _ = oracle.gradient(D, X, U, idx)
+    Xn, Vn, ln = oracle.nsgd_step(D, X, np.zeros_like(X), U, idx, 0.01, 0.0)
+    np.testing.assert_array_equal(Xn, Xs)
+    np.testing.assert_array_equal(Vn, -0.01 * g)
+    assert ln == ls
+
+
+def test_nsgd_full_batch_converges_to_min_norm_solution():
+    """Full-batch N-SGD from zero on a tiny consistent 1-source-per-row problem converges to the
+    minimum-norm least-squares solution of the dense operator (numpy.linalg.lstsq)."""
+    nt, nr, nv, ns = 6, 2, 1, 5      # condition number ~8: converged to rounding in 3000 steps
+    D = synth.random_traces((ns, nr, nt), 11)
+    Xt = synth.random_traces((nv, nr, nt), 12)
+    U = oracle.mdc_forward(D, Xt, np.arange(ns))
+    A = np.zeros((ns * nv * nt, nv * nr * nt))
+    for j in range(nv * nr * nt):
+        e = np.zeros(nv * nr * nt)
+        e[j] = 1.0
+        A[:, j] = oracle.mdc_forward(D, e.reshape(nv, nr, nt), np.arange(ns)).ravel()
+    x_ls = np.linalg.lstsq(A, U.ravel(), rcond=None)[0]
+    s2 = np.linalg.norm(A, 2) ** 2
+    X, V = np.zeros((nv, nr, nt)), np.zeros((nv, nr, nt))
+    for _ in range(3000):
+        X, V, _ = oracle.nsgd_step(D, X, V, U, np.arange(ns), 0.5 / s2, 0.9)
+    assert np.linalg.norm(X.ravel() - x_ls) <= 1e-6 * np.linalg.norm(x_ls)
+
+
+def test_causal_mute_against_loop():
+    G = synth.random_traces((3, 4, 10), 21)
+    first = np.array([[0, 3, 10, 12], [1, 0, 5, 9], [2, 2, 2, 2]])
+    M = oracle.causal_mute(G, first)
+    for v in range(3):
+        for r in range(4):
+            for t in range(10):
+                assert M[v, r, t] == (0.0 if t < first[v, r] else G[v, r, t])
+
+
+def test_nsgd_mute_and_reciprocity_keep_model_in_range():
+    """Starting from zero with a symmetric mute table, N-SGD with C = C_r C_c keeps X symmetric and zero
+    above the mute, and the unmuted samples move as the unmuted step does."""
+    n, nt, ns = 5, 16, 7
+    D = synth.random_traces((ns, n, nt), 31)
+    U = synth.random_traces((ns, n, nt), 32)
+    first = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]) * 2
+    X, V = np.zeros((n, n, nt)), np.zeros((n, n, nt))
+    for k in range(4):
+        idx = synth.random_indices(ns, 3, 40 + k)
+        X, V, _ = oracle.nsgd_step(D, X, V, U, idx, 1e-3, 0.9, recip=True, mute=first)
+        np.testing.assert_array_equal(X, np.transpose(X, (1, 0, 2)))
+        t = np.arange(nt)
+        assert np.all(X[t[None, None, :] < first[:, :, None]] == 0.0)
+    g, _, _ = oracle.gradient(D, np.zeros((n, n, nt)), U, np.array([0, 1]))
+    X1, _, _ = oracle.nsgd_step(D, np.zeros((n, n, nt)), np.zeros((n, n, nt)), U, np.array([0, 1]), 1e-3, 0.5,
+                                mute=first)
+    keep = t[None, None, :] >= first[:, :, None]
+    np.testing.assert_allclose(X1[keep], (-(1 + 0.5) * 1e-3 * g)[keep], rtol=1e-13, atol=1e-16)

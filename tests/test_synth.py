@@ -25,3 +25,15 @@ def test_batch_member_shapes():
     assert (ms[-1]["nt"], ms[-1]["nr"], ms[-1]["nv"], ms[-1]["ns"]) == (1500, 1200, 1200, 1200)
     assert len({m["seed"] for m in ms}) == 48
     assert synth.batch_members(48, seed=1000) == ms
+
+
+def test_direct_arrival_mute_keeps_true_events():
+    nt, n = 256, 40
+    p = synth.make_problem(nt, n, n, n, dx=20.0, n_reflectors=8, n_multiples=4, seed=0)
+    first = synth.direct_arrival_mute(n, n, nt, dx=20.0)
+    assert first.dtype == np.int32 and first.shape == (n, n)
+    np.testing.assert_array_equal(first, first.T)
+    t = np.arange(nt)
+    muted = t[None, None, :] < first[:, :, None]
+    assert muted.any()
+    assert np.max(np.abs(p.X_true[muted])) <= 1e-3 * np.max(np.abs(p.X_true))
