@@ -126,6 +126,32 @@ typedef struct {
 int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
               const smdd_params *params, double *loss, void *stream);
 
+/* smdd_step_ex: the same step with the N-SGD solver and the causality preconditioner.
+ * N-SGD is SGD with Nesterov momentum in the form of Sutskever et al. (2013) -- the solver the paper
+ * reports as converging fastest -- written on the look-ahead point: with g the preconditioned batch
+ * gradient evaluated at X,
+ *   V <- mu V - alpha g,   X <- X + mu V - alpha g.
+ * The causality preconditioner C_c of Eq. 4 (the space-time mask that mutes the reflection response
+ * above the direct arrival) is a per-trace first kept sample: g is set to zero on samples
+ * t < mute[v][r], so a model that starts zero there stays zero there.  The chain C = C_r C_c applies
+ * reciprocity first; with SMDD_RECIPROCITY the mute table must be symmetric (mute[v][r] == mute[r][v]),
+ * so that the two projections commute and X stays in the range of C. */
+#define SMDD_NESTEROV       16  /* smdd_step_ex only: momentum with velocity state V */
+
+typedef struct {
+    float alpha;            /* step size */
+    int flags;              /* SMDD_* bits, SMDD_NESTEROV included */
+    float mu;               /* momentum, 0 <= mu < 1 (SMDD_NESTEROV) */
+    int reserved0;          /* zero */
+    float *V;               /* SMDD_NESTEROV: velocity [nv][nr][nt] device float32, updated in place (start
+                               from zeros); NULL without SMDD_NESTEROV; never the same array as X */
+    const int32_t *mute;    /* causality mute: device int32[nv][nr], first kept sample per model trace; or NULL */
+    int reserved[4];        /* zero */
+} smdd_step_ex_params;
+
+int smdd_step_ex(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
+                 const smdd_step_ex_params *params, double *loss, void *stream);
+
 /* Forward MDC without any device allocation (the paper has no counterpart: this exists for callers
  * that may not call cudaMalloc/cudaFree -- code whose device memory is owned by another allocator or
  * pool, or loops that cannot afford an allocation's latency and implicit synchronisation).

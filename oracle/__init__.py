@@ -133,25 +133,32 @@ def default_nfft(nt: int) -> int:
     return n
 
 
-def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None) -> np.ndarray:
-    """Tier B forward: rfft along time, per-frequency matrix product, irfft, keep t < nt."""
+def kernel_spectrum(D, nfft: int | None = None) -> np.ndarray:
+    """rfft of every down-going trace, (ns, nr, nf): Appendix A transforms the kernel once."""
+    D = _f64(D)
+    return np.fft.rfft(D, n=nfft or default_nfft(D.shape[2]), axis=-1)
+
+
+def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None, Dh=None) -> np.ndarray:
+    """Tier B forward: rfft along time, per-frequency matrix product, irfft, keep t < nt.
+    Dh: the kernel spectrum of D from kernel_spectrum (same nfft), or None to transform D[idx] here."""
     D, X = _f64(D), _f64(X)
     nt = D.shape[2]
     nfft = nfft or default_nfft(nt)
     assert nfft >= 2 * nt - 1
-    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
+    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1) if Dh is None else Dh[np.asarray(idx)]   # (nb, nr, nf)
     Xh = np.fft.rfft(X, n=nfft, axis=-1)                            # (nv, nr, nf)
     Uh = np.matmul(Dh.transpose(2, 0, 1), Xh.transpose(2, 1, 0)).transpose(1, 2, 0)   # per f: [nb x nr][nr x nv]
     return scale * np.fft.irfft(Uh, n=nfft, axis=-1)[..., :nt]
 
 
-def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None) -> np.ndarray:
+def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None, Dh=None) -> np.ndarray:
     """Tier B adjoint: spectra of the residual times the conjugate down-going spectra, summed over the batch."""
     D, R = _f64(D), _f64(R)
     nt = D.shape[2]
     nfft = nfft or default_nfft(nt)
     assert nfft >= 2 * nt - 1
-    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1)          # (nb, nr, nf)
+    Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1) if Dh is None else Dh[np.asarray(idx)]   # (nb, nr, nf)
     Rh = np.fft.rfft(R, n=nfft, axis=-1)                            # (nb, nv, nf)
     Gh = np.matmul(Rh.transpose(2, 1, 0), np.conj(Dh).transpose(2, 0, 1)).transpose(1, 2, 0)  # per f: [nv x nb][nb x nr]
     return scale * np.fft.irfft(Gh, n=nfft, axis=-1)[..., :nt]
@@ -173,19 +180,21 @@ def loss(R) -> float:
     return 0.5 * float(np.sum(R * R))
 
 
-def gradient(D, X, U_obs, idx, scale: float = 1.0, fft: bool = False):
-    """Mini-batch gradient of Eq. 6: g_B = P_B^H (P_B X - U_obs[idx]).  Returns (g, loss, residual)."""
+def gradient(D, X, U_obs, idx, scale: float = 1.0, fft: bool = False, Dh=None):
+    """Mini-batch gradient of Eq. 6: g_B = P_B^H (P_B X - U_obs[idx]).  Returns (g, loss, residual).
+    Dh (fft only): the precomputed kernel spectrum."""
     idx = np.asarray(idx)
-    fwd = mdc_forward_fft if fft else mdc_forward
-    adj = mdc_adjoint_fft if fft else mdc_adjoint
-    R = fwd(D, X, idx, scale) - _f64(U_obs)[idx]
-    return adj(D, R, idx, scale), loss(R), R
+    if fft:
+        R = mdc_forward_fft(D, X, idx, scale, Dh=Dh) - _f64(U_obs)[idx]
+        return mdc_adjoint_fft(D, R, idx, scale, Dh=Dh), loss(R), R
+    R = mdc_forward(D, X, idx, scale) - _f64(U_obs)[idx]
+    return mdc_adjoint(D, R, idx, scale), loss(R), R
 
 
 def sgd_step(D, X, U_obs, idx, alpha: float, *, recip: bool = False, scale: float = 1.0,
-             fft: bool = False):
+             fft: bool = False, Dh=None):
     """One stochastic MDD step (SGD): X <- X - alpha * C(g_B), C = C_r or identity.  Returns (X_new, loss)."""
-    g, l, _ = gradient(D, X, U_obs, idx, scale, fft)
+    g, l, _ = gradient(D, X, U_obs, idx, scale, fft, Dh)
     if recip:
         g = reciprocity(g)
     return _f64(X) - alpha * g, l
@@ -196,9 +205,10 @@ def run_epochs(D, X0, U_obs, batches, alpha: float, *, recip: bool = False, scal
     """Run the given epochs of batches (batches[epoch][step] -> source indices).  Returns (X, losses)."""
     X = _f64(X0).copy()
     losses = []
+    Dh = kernel_spectrum(D) if fft else None
     for epoch in batches:
         for idx in epoch:
-            X, l = sgd_step(D, X, U_obs, idx, alpha, recip=recip, scale=scale, fft=fft)
+            X, l = sgd_step(D, X, U_obs, idx, alpha, recip=recip, scale=scale, fft=fft, Dh=Dh)
             losses.append(l)
     return X, losses
 

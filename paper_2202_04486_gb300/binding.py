@@ -29,6 +29,7 @@ SMDD_RECIPROCITY = 1
 SMDD_KEEP_XHAT = 2
 SMDD_REUSE_XHAT = 4
 SMDD_UOBS_GATHERED = 8
+SMDD_NESTEROV = 16
 
 MDC_NUM_STAGES = 7
 
@@ -44,7 +45,7 @@ EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
-    "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune",
+    "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex",
     "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy",
 )
 
@@ -57,6 +58,11 @@ class MDCError(RuntimeError):
 
 class smdd_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class smdd_step_ex_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("mu", ctypes.c_float), ("reserved0", ctypes.c_int),
+                ("V", ctypes.c_void_p), ("mute", ctypes.c_void_p), ("reserved", ctypes.c_int * 4)]
 
 
 class mdc_config(ctypes.Structure):
@@ -101,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_stage_name.argtypes = [i]
     lib.mdc_stage_name.restype = ctypes.c_char_p
     lib.mdc_forward_static.argtypes = [i, i, i, i, f, vp, vp, vp, i, vp, vp, vp]
+    lib.smdd_step_ex.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(smdd_step_ex_params), vp, vp]
     lib.mdc_plan_get_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
     lib.mdc_plan_set_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
     lib.mdc_plan_autotune.argtypes = [vp, i, i, i, ctypes.POINTER(mdc_config), vp]
@@ -203,6 +210,19 @@ def smdd_step(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor
     _check(load_library().smdd_step(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
                                     _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
                                     ctypes.byref(p), lp, _stream_ptr(stream)), "smdd_step")
+
+
+def smdd_step_ex(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor, alpha: float, flags: int = 0,
+                 V: torch.Tensor | None = None, mu: float = 0.0, mute: torch.Tensor | None = None,
+                 loss: torch.Tensor | None = None, stream=None) -> None:
+    """N-SGD (flags with SMDD_NESTEROV and a velocity V) and/or the causality mute (int32 [nv][nr])."""
+    p = smdd_step_ex_params(float(alpha), int(flags), float(mu), 0,
+                            None if V is None else _dev(V, "V", torch.float32, tuple(X.shape)).value,
+                            None if mute is None else _dev(mute, "mute", torch.int32, (X.shape[0], X.shape[1])).value)
+    lp = ctypes.c_void_p(0) if loss is None else _dev(loss, "loss", torch.float64)
+    _check(load_library().smdd_step_ex(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
+                                       _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
+                                       ctypes.byref(p), lp, _stream_ptr(stream)), "smdd_step_ex")
 
 
 def mdc_plan_sync_status(plan: int) -> int:

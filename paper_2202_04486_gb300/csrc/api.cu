@@ -430,21 +430,16 @@ int mdc_adjoint(mdc_plan_t p, const float *R, const int32_t *idx, int nb, float 
     return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
 }
 
-int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb, const smdd_params *prm,
-              double *loss, void *stream) {
-    int rc = check_common(p, X, U_obs, idx, nb);
-    if (rc) return rc;
-    if (!prm) return MDC_ERR_INVALID_ARG;
-    const int flags = prm->flags;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
-        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
-    if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
-    const bool recip = flags & SMDD_RECIPROCITY;
-    if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
-    DeviceGuard dg(p->device);
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
 
+namespace {
+
+// One step; SGD when vel is null, N-SGD otherwise; mute: causality table or null.  Arguments checked
+// by the callers.
+int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb, float alpha, int flags,
+              float *vel, float mu, const int32_t *mute, double *loss, cudaStream_t st) {
+    int rc = MDC_OK;
+    const bool recip = flags & SMDD_RECIPROCITY;
     // a1: model spectra (or the ones left by the previous step's fused update)
     if (!((flags & SMDD_REUSE_XHAT) && p->xhat_for == X)) {
         if ((rc = rfft_model(p, X, st))) return rc;
@@ -478,13 +473,61 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         FftArgs a = base_fft(p);
         a.g = model_grid(p, p->nv);
         a.tout = X;
-        a.vec = vec4_ok(p->nt, X);
+        a.vec = vec4_ok(p->nt, X) && (vel == nullptr || vec4_ok(p->nt, vel));
         a.spec = p->Xh;
-        a.alpha = prm->alpha;
+        a.alpha = alpha;
+        a.vel = vel;
+        a.mu = mu;
+        a.mute = mute;
+        if (vel || mute) {   // the momentum / mute update is built for the default radix order only
+            a.variant = 0;
+            a.tw = p->tw;
+        }
         if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;
         if (keep) p->xhat_for = X;
     }
     return MDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb, const smdd_params *prm,
+              double *loss, void *stream) {
+    int rc = check_common(p, X, U_obs, idx, nb);
+    if (rc) return rc;
+    if (!prm) return MDC_ERR_INVALID_ARG;
+    const int flags = prm->flags;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
+    if ((flags & SMDD_RECIPROCITY) && p->nr != p->nv) return MDC_ERR_SHAPE;
+    DeviceGuard dg(p->device);
+    return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags, nullptr, 0.f, nullptr, loss, (cudaStream_t)stream);
+}
+
+int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb,
+                 const smdd_step_ex_params *prm, double *loss, void *stream) {
+    int rc = check_common(p, X, U_obs, idx, nb);
+    if (rc) return rc;
+    if (!prm) return MDC_ERR_INVALID_ARG;
+    const int flags = prm->flags;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_NESTEROV))
+        return MDC_ERR_INVALID_ARG;
+    if (prm->reserved0 != 0) return MDC_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
+    const bool nesterov = flags & SMDD_NESTEROV;
+    if (nesterov && (!prm->V || !(prm->mu >= 0.f && prm->mu < 1.f))) return MDC_ERR_INVALID_ARG;
+    if (!nesterov && prm->V) return MDC_ERR_INVALID_ARG;
+    if (prm->V == X) return MDC_ERR_INVALID_ARG;
+    if ((flags & SMDD_RECIPROCITY) && p->nr != p->nv) return MDC_ERR_SHAPE;
+    DeviceGuard dg(p->device);
+    return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags & ~SMDD_NESTEROV, nesterov ? prm->V : nullptr,
+                     nesterov ? prm->mu : 0.f, prm->mute, loss, (cudaStream_t)stream);
 }
 
 int mdc_plan_get_config(mdc_plan_t p, mdc_config *cfg) {

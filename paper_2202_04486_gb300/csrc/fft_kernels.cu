@@ -128,6 +128,20 @@ __device__ __forceinline__ void pairs_to_regs(const float4 (&h)[NPAIR], float2 (
         }
 }
 
+// read 4 time samples starting at i0 (zero outside [0, nt))
+__device__ __forceinline__ float4 load_quad(const float *y, int i0, int nt, bool vec) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vec && i0 + 3 < nt) {
+        v = *reinterpret_cast<const float4 *>(y + i0);
+    } else {
+        if (i0 < nt) v.x = y[i0];
+        if (i0 + 1 < nt) v.y = y[i0 + 1];
+        if (i0 + 2 < nt) v.z = y[i0 + 2];
+        if (i0 + 3 < nt) v.w = y[i0 + 3];
+    }
+    return v;
+}
+
 // write 4 time samples starting at i0 (window [0, nt))
 __device__ __forceinline__ void store_quad(float *y, int i0, int nt, bool vec, float4 v) {
     if (vec && i0 + 3 < nt) {
@@ -283,9 +297,10 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     }
 }
 
-// SGD update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g;  optionally Gh <- rfft(X_new) (in place).
+// Update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g (SGD), or with the causality mute and/or Nesterov
+// momentum (see the else branch);  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
-template <int M, int V, bool KEEP>
+template <int M, int V, bool KEEP, bool EXT>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
@@ -301,22 +316,57 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
     float2 v[FFT_P];
     irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
     const float nas = -a.alpha * a.s;
+    if constexpr (!EXT) {
+        // SGD: X <- X - alpha g
 #pragma unroll
-    for (int qq = 0; qq < QQ; ++qq)
+        for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
-        for (int r = 0; r < R / 2; ++r) {
-            const int hs = qq * (R / 2) + r;
-            const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
-            const float2 g0 = v[(2 * qq) * R + r], g1 = v[(2 * qq + 1) * R + r];
-            const float4 xv = xo[hs];
-            float4 z;
-            z.x = (i0 < a.nt) ? fmaf(nas, g0.x, xv.x) : 0.f;
-            z.y = (i0 + 1 < a.nt) ? fmaf(nas, g0.y, xv.y) : 0.f;
-            z.z = (i0 + 2 < a.nt) ? fmaf(nas, g1.x, xv.z) : 0.f;
-            z.w = (i0 + 3 < a.nt) ? fmaf(nas, g1.y, xv.w) : 0.f;
-            if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
-            xo[hs] = z;
-        }
+            for (int r = 0; r < R / 2; ++r) {
+                const int hs = qq * (R / 2) + r;
+                const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
+                const float2 g0 = v[(2 * qq) * R + r], g1 = v[(2 * qq + 1) * R + r];
+                const float4 xv = xo[hs];
+                float4 z;
+                z.x = (i0 < a.nt) ? fmaf(nas, g0.x, xv.x) : 0.f;
+                z.y = (i0 + 1 < a.nt) ? fmaf(nas, g0.y, xv.y) : 0.f;
+                z.z = (i0 + 2 < a.nt) ? fmaf(nas, g1.x, xv.z) : 0.f;
+                z.w = (i0 + 3 < a.nt) ? fmaf(nas, g1.y, xv.w) : 0.f;
+                if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
+                xo[hs] = z;
+            }
+    } else {
+        // causality mute (the step is zero before the first kept sample) and, with a velocity,
+        // Nesterov momentum on the look-ahead point: V <- mu V + step, X <- X + mu V + step
+        const int first = (a.mute && c.valid) ? __ldg(a.mute + (long long)c.j * a.g.ni + c.i) : 0;
+        float *vp = (a.vel && c.valid) ? a.vel + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : nullptr;
+#pragma unroll
+        for (int qq = 0; qq < QQ; ++qq)
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) {
+                const int hs = qq * (R / 2) + r;
+                const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
+                const float2 g0 = v[(2 * qq) * R + r], g1 = v[(2 * qq + 1) * R + r];
+                const float4 xv = xo[hs];
+                const float gk[4] = {g0.x, g0.y, g1.x, g1.y}, xk[4] = {xv.x, xv.y, xv.z, xv.w};
+                float4 vv = vp ? load_quad(vp, i0, a.nt, a.vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float vk[4] = {vv.x, vv.y, vv.z, vv.w}, zk[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float st = (i0 + k >= first) ? nas * gk[k] : 0.f;
+                    if (vp) {
+                        vk[k] = fmaf(a.mu, vk[k], st);
+                        zk[k] = fmaf(a.mu, vk[k], xk[k] + st);
+                    } else {
+                        zk[k] = xk[k] + st;
+                    }
+                    if (i0 + k >= a.nt) zk[k] = 0.f;
+                }
+                const float4 z = make_float4(zk[0], zk[1], zk[2], zk[3]);
+                if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
+                if (vp) store_quad(vp, i0, a.nt, a.vec, make_float4(vk[0], vk[1], vk[2], vk[3]));
+                xo[hs] = z;
+            }
+    }
     if constexpr (KEEP) {
         pairs_to_regs<M, V>(xo, v);
         team_sync<T>();
@@ -427,9 +477,11 @@ static cudaError_t prepare_m() {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rfft<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_irfft_out<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residual<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         });
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return e;
 }
 
@@ -475,11 +527,18 @@ cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
-        with_variant<MM>(a.variant, [&](auto vc) {
-            constexpr int V = decltype(vc)::value;
-            if (keep) k_update<MM, V, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
-            else k_update<MM, V, false><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
-        });
+        if (a.vel || a.mute) {
+            // momentum / causality mute: radix order 0 only (the caller passes its twiddle table)
+            if (a.variant != 0) return cudaErrorInvalidValue;
+            if (keep) k_update<MM, 0, true, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+            else k_update<MM, 0, false, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+        } else {
+            with_variant<MM>(a.variant, [&](auto vc) {
+                constexpr int V = decltype(vc)::value;
+                if (keep) k_update<MM, V, true, false><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+                else k_update<MM, V, false, false><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
+            });
+        }
     });
     return cudaGetLastError();
 }

@@ -164,6 +164,12 @@ __host__ __device__ constexpr int padi(int i) { return i + 2 * (i >> 4); }
 #ifndef SMDD_FFT_MINB
 #define SMDD_FFT_MINB 3
 #endif
+#ifndef SMDD_FFT_MINB_LARGE          // the same for M >= 1024 (teams of 64 threads or more)
+#define SMDD_FFT_MINB_LARGE SMDD_FFT_MINB
+#endif
+#ifndef SMDD_FFT_NAMED_BAR           // 1: teams of more than one warp sync on their own named barrier
+#define SMDD_FFT_NAMED_BAR 0
+#endif
 
 template <int M>
 struct Team {
@@ -176,14 +182,25 @@ struct Team {
     // 16/TR bins that a half-warp touches in the tile loads / stores fall on 16 distinct bank pairs
     static constexpr int STRIDE = padi(M) + (TR >= 8 ? 2 : 16 / TR);
     static constexpr size_t SMEM = (size_t)TR * STRIDE * sizeof(float2);
+    static_assert(T <= 32 || TR <= 15, "at most 15 named team barriers");
     // resident CTAs per SM asked of the compiler: never below ~80 registers per thread
-    static constexpr int MINB = (768 / THREADS) < 1 ? 1 : ((768 / THREADS) < SMDD_FFT_MINB ? 768 / THREADS : SMDD_FFT_MINB);
+    static constexpr int MINB_ASK = M >= 1024 ? SMDD_FFT_MINB_LARGE : SMDD_FFT_MINB;
+    static constexpr int MINB = (768 / THREADS) < 1 ? 1 : ((768 / THREADS) < MINB_ASK ? 768 / THREADS : MINB_ASK);
 };
 
+// Synchronise the T threads of one trace's team (team k = threads [kT, (k+1)T) of the CTA).  Every
+// thread of a team reaches the same sequence of team syncs.
 template <int T>
 __device__ __forceinline__ void team_sync() {
-    if constexpr (T <= 32) __syncwarp();
-    else __syncthreads();
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else if constexpr (SMDD_FFT_NAMED_BAR) {
+        static_assert(T % 32 == 0, "named barriers count whole warps");
+        // barrier 0 is __syncthreads; teams use 1..TR (TR <= 15 for every team size here)
+        asm volatile("bar.sync %0, %1;\n" ::"r"(1 + (int)(threadIdx.x / T)), "n"(T) : "memory");
+    } else {
+        __syncthreads();
+    }
 }
 
 __device__ __forceinline__ float4 lds4(const float2 *p) { return *reinterpret_cast<const float4 *>(p); }

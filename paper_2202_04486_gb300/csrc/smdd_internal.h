@@ -43,6 +43,11 @@ struct FftArgs {
     double *loss;
     int *status;
     int variant;             // radix-order variant of the FFT plan (0 or 1, see fft_radix)
+    // update: Nesterov velocity (null for SGD), momentum, causality mute (first kept sample per
+    // model trace, [nv][nr]; null for none)
+    float *vel;
+    float mu;
+    const int32_t *mute;
 };
 
 struct GemmArgs {

@@ -385,3 +385,13 @@ def test_nsgd_mute_and_reciprocity_keep_model_in_range():
                                 mute=first)
     keep = t[None, None, :] >= first[:, :, None]
     np.testing.assert_allclose(X1[keep], (-(1 + 0.5) * 1e-3 * g)[keep], rtol=1e-13, atol=1e-16)
+
+
+def test_tier_b_with_precomputed_kernel_spectrum():
+    D = synth.random_traces((9, 5, 40), 61)
+    X = synth.random_traces((4, 5, 40), 62)
+    R = synth.random_traces((3, 4, 40), 63)
+    idx = np.array([7, 2, 2])
+    Dh = oracle.kernel_spectrum(D)
+    np.testing.assert_array_equal(oracle.mdc_forward_fft(D, X, idx, Dh=Dh), oracle.mdc_forward_fft(D, X, idx))
+    np.testing.assert_array_equal(oracle.mdc_adjoint_fft(D, R, idx, Dh=Dh), oracle.mdc_adjoint_fft(D, R, idx))
