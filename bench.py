@@ -268,7 +268,8 @@ def run_gpu(args, rank, world, w):
         rms = U_obs.pow(2).mean().sqrt()
         U_obs += w["noise"] * rms * torch.from_numpy(p.noise.astype(np.float32)).to(dev)
     gen.close()
-    del X_true
+    if args.fixed_error_epochs <= 0:
+        del X_true
 
     prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
     plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
@@ -434,6 +435,8 @@ def run_gpu(args, rank, world, w):
         "wall_s_timed_region": round(wall, 4),
         "loss_first_last": [float(losses[0]), float(losses[-1])],
     }
+    if args.fixed_error_epochs > 0:
+        out["fixed_error"] = precision_comparison(args, dev, D, U_obs, X_true, w, rank)
     if world == 1 or rank == 0:
         D64 = p.D.astype(np.float32).astype(np.float64)
         Xs = np.zeros((nv, nr, nt))
@@ -442,6 +445,56 @@ def run_gpu(args, rank, world, w):
         out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": sample, "s_per_step_extrapolated": round(t_step, 3)}
     return out
+
+
+def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
+    """FP32 products against split-BF16 products at the same final-model error: both run the same
+    epochs from the same batches (autotuned configurations when --autotune); the model error is the
+    relative L2 distance to the true model, and the BF16x3 path runs until its error is at most the FP32
+    path's (or twice the epochs).  Device time of the steps only."""
+    import torch
+
+    from paper_2202_04486_gb300 import binding
+
+    nt, nr, nv, ns, nb = w["nt"], w["nr"], w["nv"], w["ns"], w["nb"]
+    recip = bool(w["reciprocity"])
+    n_ep = args.fixed_error_epochs
+    batches = synth.epoch_batches(ns, nb, 2 * n_ep, seed=100 + rank)
+    idx_dev = [[torch.from_numpy(b).to(dev) for b in ep] for ep in batches]
+    xt_norm = X_true.double().norm().item()
+    res = {}
+    for name, prec in (("fp32", binding.MDC_PREC_FP32), ("bf16x3", binding.MDC_PREC_BF16X3)):
+        plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
+        flags = binding.SMDD_RECIPROCITY if recip else 0
+        cfg = plan.autotune(nb, flags, reps=3) if args.autotune else plan.get_config()
+        alpha = 0.5 * 2.0 / plan.sigma2_max(60)
+        X = torch.zeros((nv, nr, nt), device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t, steps, errs, k = 0.0, 0, [], 0
+        target = res.get("fp32", {}).get("model_error")
+        for ep in range(2 * n_ep if target is not None else n_ep):
+            e0.record()
+            for ii in idx_dev[ep]:
+                fl = flags | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+                binding.smdd_step(plan.handle, X, U_obs, ii, alpha, fl)
+                k += 1
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+            steps += len(idx_dev[ep])
+            errs.append((X.double() - X_true.double()).norm().item() / xt_norm)
+            if target is not None and ep + 1 >= n_ep and errs[-1] <= target:
+                break
+        if plan.sync_status() != binding.MDC_OK:
+            raise RuntimeError("device status after the precision comparison")
+        res[name] = {"epochs": len(errs), "steps": steps, "model_error": errs[-1], "device_s": round(t, 4),
+                     "steps_per_s": round(steps / t, 2), "kernel_config": cfg}
+        plan.close()
+    res["bf16x3_vs_fp32_steps_per_s"] = round(res["bf16x3"]["steps_per_s"] / res["fp32"]["steps_per_s"], 3)
+    res["bf16x3_vs_fp32_time_to_error"] = round(res["fp32"]["device_s"] / res["bf16x3"]["device_s"], 3)
+    res["definition"] = ("same batches from X = 0; model error = ||X - X_true|| / ||X_true||; BF16x3 runs until "
+                         "its error <= the FP32 error after the FP32 epochs; device time of the steps")
+    return res
 
 
 # ------------------------------------------------------------------------------------------------
@@ -687,6 +740,8 @@ def main():
     ap.add_argument("--batch-largest", type=int, default=1,
                     help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")
     ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
+    ap.add_argument("--fixed-error-epochs", type=int, default=0,
+                    help="also compare FP32 and BF16x3 products at the same final-model error after this many epochs")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"],
                     help="arithmetic of the per-frequency products (the FFTs are FP32 in both)")
     args = ap.parse_args()

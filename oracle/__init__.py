@@ -18,7 +18,8 @@ down-going field, a dense operator built from scipy Toeplitz blocks, the adjoint
 finite-sum identity of Eq. 5/6, the Landweber toy of Eq. 11 (sigma^2 = 53.0256), the spectral bound on
 the operator norm, SGD converging to the least-squares solution of a tiny consistent problem, and for
 N-SGD: the equivalence of the look-ahead form with Sutskever's form, mu = 0 giving SGD, and convergence
-to the minimum-norm least-squares solution; the causality mute against an explicit loop.
+to the minimum-norm least-squares solution; the causality mute against an explicit loop; LSQR against
+scipy's implementation and the least-squares solution.
 
 Readings of the paper taken here (each is also listed in the design notes):
   * scale: the receiver integral of Eq. 1 is a plain sum over receivers times `scale` (default 1).
@@ -249,6 +250,58 @@ def nsgd_step(D, X, V, U_obs, idx, alpha: float, mu: float, *, recip: bool = Fal
     V_new = mu * _f64(V) - alpha * g
     X_new = _f64(X) + mu * V_new - alpha * g
     return X_new, V_new, l
+
+
+def lsqr(apply_A, apply_At, b, x0, n_iter: int):
+    """LSQR (Paige & Saunders 1982, the bidiagonalisation algorithm of their Section 4) for
+    min ||A x - b||, the full-gradient MDD solver the paper compares against.  apply_A / apply_At are
+    the operator and its adjoint on arrays of the shapes of x and b.  Starts from x0 (the iteration
+    solves for the correction).  Returns (x, residual-norm estimates phi_bar_1 .. phi_bar_{n+1})."""
+    x = _f64(x0).copy()
+    u = _f64(b) - apply_A(x)
+    beta = np.linalg.norm(u)
+    u = u / beta if beta > 0 else u
+    v = apply_At(u)
+    alpha = np.linalg.norm(v)
+    v = v / alpha if alpha > 0 else v
+    w = v.copy()
+    phi_bar, rho_bar = beta, alpha
+    norms = [phi_bar]
+    for _ in range(n_iter):
+        # continue the bidiagonalisation
+        u = apply_A(v) - alpha * u
+        beta = np.linalg.norm(u)
+        if beta > 0:
+            u = u / beta
+        v = apply_At(u) - beta * v
+        alpha = np.linalg.norm(v)
+        if alpha > 0:
+            v = v / alpha
+        # plane rotation eliminating the subdiagonal beta
+        rho = np.hypot(rho_bar, beta)
+        c, s = rho_bar / rho, beta / rho
+        theta = s * alpha
+        rho_bar = -c * alpha
+        phi = c * phi_bar
+        phi_bar = s * phi_bar
+        # solution and search direction
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        norms.append(phi_bar)
+    return x, norms
+
+
+def mdc_lsqr(D, X0, U_obs, n_iter: int, *, recip: bool = False, mute=None, scale: float = 1.0):
+    """Full-gradient MDD by LSQR on the preconditioned operator P C (Eq. 3-4): every source at once,
+    x = C z with z from LSQR on A = P C, C = C_r C_c (each optional); the operator through Tier B.
+    X0 must lie in the range of C (e.g. zero).  Returns (X, residual-norm estimates)."""
+    D = _f64(D)
+    ns = D.shape[0]
+    idx = np.arange(ns)
+    Dh = kernel_spectrum(D)
+    fwd = lambda X: mdc_forward_fft(D, X, idx, scale, Dh=Dh)
+    adj = lambda R: precondition(mdc_adjoint_fft(D, R, idx, scale, Dh=Dh), recip=recip, mute=mute)
+    return lsqr(fwd, adj, _f64(U_obs), X0, n_iter)
 
 
 def steps_per_epoch(ns: int, nb: int) -> int:

@@ -395,3 +395,36 @@ def test_tier_b_with_precomputed_kernel_spectrum():
     Dh = oracle.kernel_spectrum(D)
     np.testing.assert_array_equal(oracle.mdc_forward_fft(D, X, idx, Dh=Dh), oracle.mdc_forward_fft(D, X, idx))
     np.testing.assert_array_equal(oracle.mdc_adjoint_fft(D, R, idx, Dh=Dh), oracle.mdc_adjoint_fft(D, R, idx))
+
+
+# ------------------------------------------------------------------------------------------------
+# LSQR (Paige & Saunders), the full-gradient baseline
+# ------------------------------------------------------------------------------------------------
+def test_lsqr_matches_scipy_iterates():
+    from scipy.sparse.linalg import lsqr as scipy_lsqr
+    rng = np.random.default_rng(71)
+    A = rng.standard_normal((30, 12)) @ np.diag(np.linspace(3, 0.2, 12))
+    b = rng.standard_normal(30)
+    for k in (1, 3, 7, 10, 20):   # (k = 12 = n ends the Krylov space: both are then ill-conditioned in beta ~ 0)
+        x, norms = oracle.lsqr(lambda z: A @ z, lambda r: A.T @ r, b, np.zeros(12), k)
+        xs = scipy_lsqr(A, b, atol=0, btol=0, conlim=0, iter_lim=k)[0]
+        np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-12)
+        assert abs(norms[-1] - np.linalg.norm(b - A @ x)) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_lsqr_on_mdc_reaches_least_squares_and_keeps_preconditioned_range():
+    nt, n, ns = 8, 2, 3
+    D = synth.random_traces((ns, n, nt), 81)
+    U = synth.random_traces((ns, n, nt), 82)
+    nx = n * n * nt
+    A = np.zeros((ns * n * nt, nx))
+    for j in range(nx):
+        e = np.zeros(nx)
+        e[j] = 1.0
+        A[:, j] = oracle.mdc_forward(D, e.reshape(n, n, nt), np.arange(ns)).ravel()
+    X, norms = oracle.mdc_lsqr(D, np.zeros((n, n, nt)), U, nx + 5)
+    x_ls = np.linalg.lstsq(A, U.ravel(), rcond=None)[0]
+    assert np.linalg.norm(A @ X.ravel() - U.ravel()) <= (1 + 1e-8) * np.linalg.norm(A @ x_ls - U.ravel())
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(norms, norms[1:]))     # monotone residual estimates
+    Xr, _ = oracle.mdc_lsqr(D, np.zeros((n, n, nt)), U, 6, recip=True)
+    np.testing.assert_allclose(Xr, np.transpose(Xr, (1, 0, 2)), rtol=0, atol=1e-12)
