@@ -152,6 +152,22 @@ typedef struct {
 int smdd_step_ex(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
                  const smdd_step_ex_params *params, double *loss, void *stream);
 
+/* Full-gradient MDD by LSQR (Paige & Saunders 1982): the baseline the paper compares stochastic MDD
+ * against (the Synthetic OBC example's "10 iterations of LSQR"), on the preconditioned operator
+ * A = P C with P the MDC over every source (Eq. 3) and C = C_r C_c (Eq. 4; each optional):
+ *   X     : [nv][nr][nt] device float32; the starting model on entry (it must lie in the range of C,
+ *           e.g. zero), the LSQR solution after n_iter iterations on return.
+ *   U_obs : [ns][nv][nt] device float32.
+ *   flags : 0 or SMDD_RECIPROCITY.   mute : causality table as in smdd_step_ex, or NULL.
+ *   norms : device float64[n_iter + 1] (or NULL): LSQR's estimates of ||U_obs - A X|| at the start and
+ *           after every iteration.
+ * The plan must have been made with nb_max >= ns (all sources form one batch).  Vectors are FP32, norms
+ * and the recurrence FP64, all on the device: the call enqueues a fixed sequence of launches and does not
+ * synchronise.  The first call allocates a workspace of 2 data-size and 3 model-size FP32 vectors, kept
+ * by the plan until it is destroyed (that call must not be made during a stream capture). */
+int smdd_lsqr(mdc_plan_t plan, float *X, const float *U_obs, int n_iter, int flags, const int32_t *mute,
+              double *norms, void *stream);
+
 /* Forward MDC without any device allocation (the paper has no counterpart: this exists for callers
  * that may not call cudaMalloc/cudaFree -- code whose device memory is owned by another allocator or
  * pool, or loops that cannot afford an allocation's latency and implicit synchronisation).
@@ -205,6 +221,13 @@ int mdc_plan_set_config(mdc_plan_t plan, const mdc_config *cfg);
  * Uses temporary device memory (cudaMalloc), overwrites the plan's spectral workspaces, synchronises
  * the stream, and must not be called during a stream capture. */
 int mdc_plan_autotune(mdc_plan_t plan, int nb, int flags, int reps, mdc_config *best, void *stream);
+
+/* Band limit (approximate; the paper has no counterpart): only the bins f < nf_active take part in the
+ * per-frequency products of every later call, the others get zero products (the FFTs still run at full
+ * length, so the operator is the exact one restricted to the band).  For band-limited data -- the Ricker
+ * wavelet of the synthetic workloads has no energy above ~3 f0 -- this skips the empty bins; the error
+ * against the exact operator is the energy of the data above the band.  0 (or >= nf) restores every bin. */
+int mdc_plan_set_band(mdc_plan_t plan, int nf_active);
 
 /* ---------------------------------------------------------------------------------------------
  * Many independent problems.  The paper solves one MDD problem at a time and has no counterpart;

@@ -140,9 +140,10 @@ def kernel_spectrum(D, nfft: int | None = None) -> np.ndarray:
     return np.fft.rfft(D, n=nfft or default_nfft(D.shape[2]), axis=-1)
 
 
-def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None, Dh=None) -> np.ndarray:
+def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None, Dh=None, band: int | None = None) -> np.ndarray:
     """Tier B forward: rfft along time, per-frequency matrix product, irfft, keep t < nt.
-    Dh: the kernel spectrum of D from kernel_spectrum (same nfft), or None to transform D[idx] here."""
+    Dh: the kernel spectrum of D from kernel_spectrum (same nfft), or None to transform D[idx] here.
+    band: only bins f < band take part in the products (the band-limited variant), None for all."""
     D, X = _f64(D), _f64(X)
     nt = D.shape[2]
     nfft = nfft or default_nfft(nt)
@@ -150,10 +151,12 @@ def mdc_forward_fft(D, X, idx, scale: float = 1.0, nfft: int | None = None, Dh=N
     Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1) if Dh is None else Dh[np.asarray(idx)]   # (nb, nr, nf)
     Xh = np.fft.rfft(X, n=nfft, axis=-1)                            # (nv, nr, nf)
     Uh = np.matmul(Dh.transpose(2, 0, 1), Xh.transpose(2, 1, 0)).transpose(1, 2, 0)   # per f: [nb x nr][nr x nv]
+    if band is not None:
+        Uh[..., band:] = 0.0
     return scale * np.fft.irfft(Uh, n=nfft, axis=-1)[..., :nt]
 
 
-def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None, Dh=None) -> np.ndarray:
+def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None, Dh=None, band: int | None = None) -> np.ndarray:
     """Tier B adjoint: spectra of the residual times the conjugate down-going spectra, summed over the batch."""
     D, R = _f64(D), _f64(R)
     nt = D.shape[2]
@@ -162,6 +165,8 @@ def mdc_adjoint_fft(D, R, idx, scale: float = 1.0, nfft: int | None = None, Dh=N
     Dh = np.fft.rfft(D[np.asarray(idx)], n=nfft, axis=-1) if Dh is None else Dh[np.asarray(idx)]   # (nb, nr, nf)
     Rh = np.fft.rfft(R, n=nfft, axis=-1)                            # (nb, nv, nf)
     Gh = np.matmul(Rh.transpose(2, 1, 0), np.conj(Dh).transpose(2, 0, 1)).transpose(1, 2, 0)  # per f: [nv x nb][nb x nr]
+    if band is not None:
+        Gh[..., band:] = 0.0
     return scale * np.fft.irfft(Gh, n=nfft, axis=-1)[..., :nt]
 
 

@@ -45,7 +45,7 @@ EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
-    "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex",
+    "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex", "smdd_lsqr", "mdc_plan_set_band",
     "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy",
 )
 
@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_stage_name.restype = ctypes.c_char_p
     lib.mdc_forward_static.argtypes = [i, i, i, i, f, vp, vp, vp, i, vp, vp, vp]
     lib.smdd_step_ex.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(smdd_step_ex_params), vp, vp]
+    lib.smdd_lsqr.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+    lib.mdc_plan_set_band.argtypes = [vp, i]
     lib.mdc_plan_get_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
     lib.mdc_plan_set_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
     lib.mdc_plan_autotune.argtypes = [vp, i, i, i, ctypes.POINTER(mdc_config), vp]
@@ -223,6 +225,16 @@ def smdd_step_ex(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Ten
     _check(load_library().smdd_step_ex(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
                                        _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
                                        ctypes.byref(p), lp, _stream_ptr(stream)), "smdd_step_ex")
+
+
+def smdd_lsqr(plan: int, X: torch.Tensor, U_obs: torch.Tensor, n_iter: int, flags: int = 0,
+              mute: torch.Tensor | None = None, norms: torch.Tensor | None = None, stream=None) -> None:
+    """Full-gradient LSQR on every source (the plan needs nb_max >= ns); X holds the start and the result."""
+    mp = ctypes.c_void_p(0) if mute is None else _dev(mute, "mute", torch.int32, (X.shape[0], X.shape[1]))
+    npp = ctypes.c_void_p(0) if norms is None else _dev(norms, "norms", torch.float64, (n_iter + 1,))
+    _check(load_library().smdd_lsqr(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
+                                    _dev(U_obs, "U_obs", torch.float32), int(n_iter), int(flags), mp, npp,
+                                    _stream_ptr(stream)), "smdd_lsqr")
 
 
 def mdc_plan_sync_status(plan: int) -> int:
@@ -396,6 +408,10 @@ class MDCPlan:
         cur = self.get_config()
         cur.update(cfg)
         mdc_plan_set_config(self.handle, **cur)
+
+    def set_band(self, nf_active: int) -> None:
+        """Only bins f < nf_active take part in the products (0: every bin)."""
+        _check(load_library().mdc_plan_set_band(ctypes.c_void_p(self.handle), int(nf_active)), "mdc_plan_set_band")
 
     def autotune(self, nb: int, flags: int = 0, reps: int = 5) -> dict:
         return mdc_plan_autotune(self.handle, nb, flags, reps)

@@ -63,6 +63,8 @@ struct mdc_plan_s {
     int fft_variant = 0;
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
+    int nf_active = 0;           // band limit of the products (0: every bin)
+    LsqrWork *lsqr = nullptr;    // full-gradient solver workspace, allocated by the first smdd_lsqr
 };
 
 namespace {
@@ -173,6 +175,7 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.sCf = (long long)p->nv * p->ldb;
     g.outscale = 1.f;
     g.status = p->status;
+    g.nf_active = p->nf_active;
     if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
@@ -191,10 +194,45 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.sCf = (long long)p->nv * p->ldr;
     g.outscale = recip ? 0.5f : 1.f;
     g.status = p->status;
+    g.nf_active = p->nf_active;
     if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
     const int tile = p->gemm_adj == MDC_GEMM_SIMT32 ? 32 : p->gemm_adj == MDC_GEMM_SIMT64 ? 64 : 0;
     return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st, tile); });
+}
+
+int forward_impl(mdc_plan_s *p, const float *X, const int32_t *idx, int nb, float *U, cudaStream_t st) {
+    int rc;
+    p->xhat_for = nullptr;
+    if ((rc = rfft_model(p, X, st))) return rc;
+    if ((rc = gemm_forward(p, idx, nb, st))) return rc;
+    FftArgs a = base_fft(p);
+    a.g = batch_grid(p, nb);
+    a.tout = U;
+    a.vec = vec4_ok(p->nt, U);
+    a.spec = p->Uh;
+    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
+}
+
+// adjoint, with the reciprocity projection 1/2 (G + G^T) when recip
+int adjoint_impl(mdc_plan_s *p, const float *R, const int32_t *idx, int nb, float *G, bool recip, cudaStream_t st) {
+    int rc;
+    p->xhat_for = nullptr;
+    {
+        FftArgs a = base_fft(p);
+        a.g = batch_grid(p, nb);
+        a.tin = R;
+        a.vec = vec4_ok(p->nt, R);
+        a.spec = p->Uh;
+        if ((rc = launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); }))) return rc;
+    }
+    if ((rc = gemm_adjoint(p, idx, nb, recip, st))) return rc;
+    FftArgs a = base_fft(p);
+    a.g = model_grid(p, p->nv);
+    a.tout = G;
+    a.vec = vec4_ok(p->nt, G);
+    a.spec = p->Xh;
+    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
 }
 
 int check_common(mdc_plan_s *p, const void *a, const void *b, const int32_t *idx, int nb) {
@@ -362,6 +400,7 @@ int mdc_plan_destroy(mdc_plan_t p) {
         cudaEventDestroy(t.e1);
     }
     for (auto e : p->event_pool) cudaEventDestroy(e);
+    delete p->lsqr;
     delete p;
     return MDC_OK;
 }
@@ -395,39 +434,54 @@ int mdc_forward(mdc_plan_t p, const float *X, const int32_t *idx, int nb, float 
     int rc = check_common(p, X, U, idx, nb);
     if (rc) return rc;
     DeviceGuard dg(p->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    p->xhat_for = nullptr;
-    if ((rc = rfft_model(p, X, st))) return rc;
-    if ((rc = gemm_forward(p, idx, nb, st))) return rc;
-    FftArgs a = base_fft(p);
-    a.g = batch_grid(p, nb);
-    a.tout = U;
-    a.vec = vec4_ok(p->nt, U);
-    a.spec = p->Uh;
-    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
+    return forward_impl(p, X, idx, nb, U, (cudaStream_t)stream);
 }
 
 int mdc_adjoint(mdc_plan_t p, const float *R, const int32_t *idx, int nb, float *G, void *stream) {
     int rc = check_common(p, R, G, idx, nb);
     if (rc) return rc;
     DeviceGuard dg(p->device);
+    return adjoint_impl(p, R, idx, nb, G, false, (cudaStream_t)stream);
+}
+
+int smdd_lsqr(mdc_plan_t p, float *X, const float *U_obs, int n_iter, int flags, const int32_t *mute, double *norms,
+              void *stream) {
+    if (!p || !X || !U_obs || n_iter < 0) return MDC_ERR_INVALID_ARG;
+    if (flags & ~SMDD_RECIPROCITY) return MDC_ERR_INVALID_ARG;
+    const bool recip = flags & SMDD_RECIPROCITY;
+    if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
+    if (p->nbmax < p->ns) return MDC_ERR_SHAPE;
+    DeviceGuard dg(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    p->xhat_for = nullptr;
-    {
-        FftArgs a = base_fft(p);
-        a.g = batch_grid(p, nb);
-        a.tin = R;
-        a.vec = vec4_ok(p->nt, R);
-        a.spec = p->Uh;
-        if ((rc = launch_stage(p, ST_RFFT, st, [&] { return launch_rfft(p->M, a, st); }))) return rc;
+    const long long nd = (long long)p->ns * p->nv * p->nt, nm = (long long)p->nv * p->nr * p->nt;
+    if (!p->lsqr || p->lsqr->nd != nd || p->lsqr->nm != nm) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return MDC_ERR_INVALID_ARG;
+        if (!p->lsqr) p->lsqr = new (std::nothrow) LsqrWork();
+        if (!p->lsqr) return MDC_ERR_OOM;
+        if (p->lsqr->ensure(nd, nm, p->ns) != cudaSuccess) {
+            cudaGetLastError();
+            return MDC_ERR_OOM;
+        }
+        std::vector<int32_t> h(p->ns);
+        for (int i = 0; i < p->ns; ++i) h[i] = i;
+        if (cudaMemcpy(p->lsqr->idx, h.data(), p->ns * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MDC_ERR_CUDA;
     }
-    if ((rc = gemm_adjoint(p, idx, nb, false, st))) return rc;
-    FftArgs a = base_fft(p);
-    a.g = model_grid(p, p->nv);
-    a.tout = G;
-    a.vec = vec4_ok(p->nt, G);
-    a.spec = p->Xh;
-    return launch_stage(p, ST_IRFFT_OUT, st, [&] { return launch_irfft_out(p->M, a, st); });
+    LsqrWork &wk = *p->lsqr;
+    int orc = MDC_OK;
+    auto fwd = [&](const float *x, float *out) -> cudaError_t {
+        orc = forward_impl(p, x, wk.idx, p->ns, out, st);
+        return orc ? cudaErrorUnknown : cudaSuccess;
+    };
+    auto adj = [&](const float *r, float *out) -> cudaError_t {
+        orc = adjoint_impl(p, r, wk.idx, p->ns, out, recip, st);
+        return orc ? cudaErrorUnknown : cudaSuccess;
+    };
+    p->xhat_for = nullptr;
+    const cudaError_t e = lsqr_run(wk, X, U_obs, nd, nm, p->nt, n_iter, mute, norms, st, fwd, adj, &p->launches);
+    if (orc) return orc;
+    return e == cudaSuccess ? MDC_OK : MDC_ERR_CUDA;
 }
 
 }  // extern "C"
@@ -528,6 +582,13 @@ int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx,
     DeviceGuard dg(p->device);
     return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags & ~SMDD_NESTEROV, nesterov ? prm->V : nullptr,
                      nesterov ? prm->mu : 0.f, prm->mute, loss, (cudaStream_t)stream);
+}
+
+int mdc_plan_set_band(mdc_plan_t p, int nf_active) {
+    if (!p || nf_active < 0) return MDC_ERR_INVALID_ARG;
+    p->nf_active = (nf_active == 0 || nf_active >= p->nf) ? 0 : nf_active;
+    p->xhat_for = nullptr;
+    return MDC_OK;
 }
 
 int mdc_plan_get_config(mdc_plan_t p, mdc_config *cfg) {

@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(FW_THREADS, 4) k_cgemm_fwd(GemmArgs a) {
     extern __shared__ __align__(16) float2 gsm[];
     const int f = blockIdx.z;
     const int v0 = blockIdx.x * FW_ROWS, b0 = blockIdx.y * FW_NB;
+    if (a.nf_active > 0 && f >= a.nf_active) {
+        zero_tile(a.C + (long long)f * a.sCf, a.ldb, v0, FW_ROWS, b0, FW_NB, a.nv, a.nb);
+        return;
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vg = lane & 7, bg = lane >> 3;
     const float2 *Af = a.A + (long long)f * a.sAf;
@@ -240,6 +244,11 @@ __global__ void __launch_bounds__(AdjGeom<TT>::THREADS, TT == 64 ? 3 : 8) k_cgem
         rb = blockIdx.x % a.tiles_r;
     }
     const int v0 = vb * TT, r0 = rb * TT;
+    if (a.nf_active > 0 && f >= a.nf_active) {
+        zero_tile(a.C + (long long)f * a.sCf, a.ldr, v0, TT, r0, TT, a.nv, a.nr);
+        if (RECIP) zero_tile(a.C + (long long)f * a.sCf, a.ldr, r0, TT, v0, TT, a.nr, a.nv);
+        return;
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int vp = lane / G::RG, rg = lane % G::RG;
     const int vl = G::WROWS * warp + 4 * vp;     // first local row of the thread

@@ -94,6 +94,10 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     __shared__ int fail;
     uint8_t *sm = align1024(tc_raw);
     const int f = blockIdx.z, v0 = blockIdx.x * 128, b0 = blockIdx.y * NB;
+    if (a.nf_active > 0 && f >= a.nf_active) {   // above the band limit: zero products, no TMEM
+        zero_tile(a.C + (long long)f * a.sCf, a.ldb, v0, 128, b0, NB, a.nv, a.nb);
+        return;
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float2 *Af = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
@@ -170,13 +174,14 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
             umma_commit(&bars[s]);
         }
     }
-    if (!fail) {
-        const int last = nk - 1;
-        if (!mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1)) fail = 1;
-    }
-    tc_fence_after();
+    const int last = nk - 1;
+    if (!fail && !mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1)) fail = 1;
     __syncthreads();
     const bool ok = !fail;
+    // after a timeout, give products still in flight one more bounded wait before TMEM is freed
+    if (!ok) mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1);
+    tc_fence_after();
+    __syncthreads();
     // epilogue: TMEM -> shared staging [128][NB] complex -> coalesced rows of C
     float2 *out = reinterpret_cast<float2 *>(sm);
     if (ok && warp < 4) {
@@ -205,28 +210,49 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
 }
 
 // ------------------------------------------------------------------------------------------------
-// adjoint: C[f][v][r] = outscale * sum_k A'[v][k] B'[k][r] on 128 x 128 tiles, K = nb (chunks of 64):
-//   first half  A' = Rh[f][v][b] (K-major),            B' = conj(Dh[f][idx_b][r]) (N-major)
-//   second half A' = conj(Dh[f][idx_b][v]) (M-major),   B' = Rh[f][r][b] (K-major)   (reciprocity)
+// adjoint: C[f][v][r] = outscale * sum_k A'[v][k] B'[k][r] on 128 x 128 tiles, K = nb in chunks of 32:
+//   first half  A' = Rh[f][v][b],                 B' = conj(Dh[f][idx_b][r])
+//   second half A' = conj(Dh[f][idx_b][v]),       B' = Rh[f][r][b]          (reciprocity)
+// Both operands are stored MN-major (rows k, 128 contiguous m / n), so every plane is 32 x 256 bytes:
+// the kernel rows of Dh are MN-major as loaded, and the residual rows (b contiguous in HBM) are copied
+// by cp.async into a staging tile and transposed while they are split.  About 100 KB of shared memory:
+// two CTAs share an SM, one CTA's epilogue overlapping the other's loads and products; the loads of
+// the next chunk are issued before the wait for the previous chunk's products.
 // With reciprocity only the upper-triangular tiles run and the transposed tile is mirrored.
 // ------------------------------------------------------------------------------------------------
 struct TcAdj {
-    static constexpr int PLANE = 128 * 128;             // bytes: 128 rows x 64 k, or 2 atoms x 64 k x 128 B
-    static constexpr int OPER = 8 * PLANE;              // A' and B' planes
-    static constexpr int OUT = 128 * 129 * 8;           // complex staging tile, padded rows
-    static constexpr size_t SMEM = (OUT > OPER ? OUT : OPER) + 1024;
+    static constexpr int KC = 32;                       // K chunk
+    static constexpr int PLANE = 2 * KC * 128;          // bytes: 2 atoms of 64 m/n x KC rows x 128 B
+    static constexpr int OPER = 8 * PLANE;              // A' and B' planes (64 KB)
+    static constexpr int SLD = KC + 2;                  // staging row pitch in float2 (16-byte multiple)
+    static constexpr int STAGE = 128 * SLD * 8;         // residual staging tile (34 KB)
+    static constexpr int OUT = 128 * 65 * 8;            // epilogue staging: 64 columns per pass
+    static constexpr size_t BODY = (size_t)OPER + STAGE;
+    static constexpr size_t SMEM = (BODY > OUT ? BODY : OUT) + 1024;
     static constexpr uint32_t TMEM_COLS = 256;
 };
 
+__device__ __forceinline__ void cp_async16_zfill(void *smem_dst, const void *gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <bool RECIP>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_adj(GemmArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
+    using G = TcAdj;
+    constexpr int KC = G::KC;
     extern __shared__ uint8_t tc_raw[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_holder;
     __shared__ int sidx[1024];
     __shared__ int fail;
     uint8_t *sm = align1024(tc_raw);
-    uint8_t *sA = sm, *sB = sm + 4 * TcAdj::PLANE;
+    uint8_t *sA = sm, *sB = sm + 4 * G::PLANE;
+    float2 *stg = reinterpret_cast<float2 *>(sm + G::OPER);
     const int f = blockIdx.y;
     int vb, rb;
     if (RECIP) {
@@ -239,6 +265,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_adj(GemmArgs a) {
         rb = blockIdx.x % a.tiles_r;
     }
     const int v0 = vb * 128, r0 = rb * 128;
+    if (a.nf_active > 0 && f >= a.nf_active) {   // above the band limit: zero products, no TMEM
+        zero_tile(a.C + (long long)f * a.sCf, a.ldr, v0, 128, r0, 128, a.nv, a.nr);
+        if (RECIP) zero_tile(a.C + (long long)f * a.sCf, a.ldr, r0, 128, v0, 128, a.nr, a.nv);
+        return;
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float2 *Rf = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
@@ -256,106 +287,128 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_adj(GemmArgs a) {
         fail = 0;
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_holder, TcAdj::TMEM_COLS);
+    if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    constexpr uint32_t idp1 = umma_idesc(128, 128, 0, 1, 0), idn1 = umma_idesc(128, 128, 0, 1, 1);
-    constexpr uint32_t idp2 = umma_idesc(128, 128, 1, 0, 0), idn2 = umma_idesc(128, 128, 1, 0, 1);
+    constexpr uint32_t idp = umma_idesc(128, 128, 1, 1, 0), idn = umma_idesc(128, 128, 1, 1, 1);
 
-    const int nkc = (a.nb + 63) / 64;
+    const int nkc = (a.nb + KC - 1) / KC;
     const int nhalf = RECIP ? 2 : 1;
+    const int njobs = nkc * nhalf;
+    constexpr int UD = KC * 16 / TC_THREADS;            // kernel-row units (8 complex) per thread
     int phase = 0;
-    for (int kc = 0; kc < nkc && !fail; ++kc) {
-        const int k0 = kc * 64;
-        const int kn = min(64, a.nb - k0), kpad = (kn + 15) & ~15;
-        for (int half = 0; half < nhalf; ++half) {
-            if (kc > 0 || half > 0) {   // the previous MMAs must be done reading the operand planes
-                if (!mbar_wait_bounded(&bar, phase & 1)) fail = 1;
-                ++phase;
-                __syncthreads();
-                if (fail) break;
+    for (int job = 0; job < njobs; ++job) {
+        const int kc = job / nhalf, half = job % nhalf;
+        const int k0 = kc * KC;
+        const int kn = min(KC, a.nb - k0), kpad = (kn + 15) & ~15;
+        const int cr = half ? r0 : v0, ncr = half ? a.nr : a.nv;   // residual rows of this half
+        const int cd = half ? v0 : r0, ncd = half ? a.nv : a.nr;   // kernel-row columns of this half
+        // residual rows -> staging (cp.async, zero-filled past the matrix); the staging tile was
+        // released by the __syncthreads before the previous job's products
+        for (int u = tid; u < 128 * (KC / 2); u += TC_THREADS) {
+            const int row = u / (KC / 2), pr = u % (KC / 2), k = k0 + 2 * pr, rr = cr + row;
+            int bytes = 0;
+            const float2 *src = Rf;
+            if (rr < ncr && k < a.nb) {
+                bytes = (k + 1 < a.nb) ? 16 : 8;
+                src = Rf + (long long)rr * a.ldb + k;
             }
-            const int c0 = half ? r0 : v0, nc0 = half ? a.nr : a.nv;   // K-major rows: Rh rows of this block
-            const int c1 = half ? v0 : r0, nc1 = half ? a.nv : a.nr;   // MN-major columns: kernel rows at this block
-            // K-major operand: 128 rows of Rh, k in [k0, k0 + kpad)
-            for (int u = tid; u < 128 * (kpad / 8); u += TC_THREADS) {
-                const int row = u / (kpad / 8), c = u % (kpad / 8), rr = c0 + row;
-                float2 z[8];
-                load8(rr < nc0 ? Rf + (long long)rr * a.ldb : nullptr, k0 + 8 * c, a.nb, z);
-                store_planes(half ? sB : sA, row * 128 + ((c ^ (row & 7)) << 4), TcAdj::PLANE, split8(z, false));
-            }
-            // MN-major operand: kpad rows k of conj(Dh[idx_k]) at 128 columns, 2 atoms of 64
-            for (int u = tid; u < kpad * 16; u += TC_THREADS) {
-                const int k = u >> 4, ch = u & 15, at = ch >> 3, c = ch & 7;
-                const int srow = (k0 + k < a.nb) ? sidx[k0 + k] : -1;
-                float2 z[8];
-                load8(srow >= 0 ? Df + (long long)srow * a.ldr : nullptr, c1 + 64 * at + 8 * c, nc1, z);
-                store_planes(half ? sA : sB, at * (64 * 128) + k * 128 + ((c ^ (k & 7)) << 4), TcAdj::PLANE,
-                             split8(z, true));
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                for (int ks = 0; ks < kpad / 16; ++ks) {
-                    uint64_t ad[4], bd[4];
+            cp_async16_zfill(stg + row * G::SLD + 2 * pr, src, bytes);
+        }
+        // kernel rows (MN-major operand) -> registers
+        float2 zd[UD][8];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        if (!half) {
-                            ad[p] = umma_desc(smem_u32(sA + p * TcAdj::PLANE + ks * 32), 16, 1024);
-                            bd[p] = umma_desc(smem_u32(sB + p * TcAdj::PLANE + ks * 16 * 128), 64 * 128, 1024);
-                        } else {
-                            ad[p] = umma_desc(smem_u32(sA + p * TcAdj::PLANE + ks * 16 * 128), 64 * 128, 1024);
-                            bd[p] = umma_desc(smem_u32(sB + p * TcAdj::PLANE + ks * 32), 16, 1024);
-                        }
-                    }
-                    mma_complex_split(tmem, tmem + 128, ad, bd, half ? idp2 : idp1, half ? idn2 : idn1,
-                                      (kc > 0 || half > 0 || ks > 0) ? 1u : 0u);
+        for (int i = 0; i < UD; ++i) {
+            const int u = tid + i * TC_THREADS, k = u >> 4, ch = u & 15, at = ch >> 3, c = ch & 7;
+            const int srow = (k < kn) ? sidx[k0 + k] : -1;
+            load8(srow >= 0 ? Df + (long long)srow * a.ldr : nullptr, cd + 64 * at + 8 * c, ncd, zd[i]);
+        }
+        // the previous products must be done reading the planes
+        if (job > 0) {
+            if (!mbar_wait_bounded(&bar, phase & 1)) fail = 1;
+            ++phase;
+        }
+        tc_fence_after();
+        uint8_t *pD = half ? sA : sB, *pR = half ? sB : sA;
+#pragma unroll
+        for (int i = 0; i < UD; ++i) {
+            const int u = tid + i * TC_THREADS, k = u >> 4, ch = u & 15, at = ch >> 3, c = ch & 7;
+            store_planes(pD, at * (KC * 128) + k * 128 + ((c ^ (k & 7)) << 4), G::PLANE, split8(zd[i], true));
+        }
+        cp_async_commit_wait_all();
+        __syncthreads();
+        // staging -> transposed, split residual planes: thread (k, chunk) takes 8 consecutive rows
+        for (int u = tid; u < KC * 16; u += TC_THREADS) {
+            const int k = u % KC, ch = u / KC, at = ch >> 3, c = ch & 7;
+            float2 z[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) z[j] = stg[(64 * at + 8 * c + j) * G::SLD + k];
+            store_planes(pR, at * (KC * 128) + k * 128 + ((c ^ (k & 7)) << 4), G::PLANE, split8(z, false));
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (fail) break;
+        if (tid == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < kpad / 16; ++ks) {
+                uint64_t ad[4], bd[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    ad[p] = umma_desc(smem_u32(sA + p * G::PLANE + ks * 16 * 128), KC * 128, 1024);
+                    bd[p] = umma_desc(smem_u32(sB + p * G::PLANE + ks * 16 * 128), KC * 128, 1024);
                 }
-                umma_commit(&bar);
+                mma_complex_split(tmem, tmem + 128, ad, bd, idp, idn, (job > 0 || ks > 0) ? 1u : 0u);
             }
+            umma_commit(&bar);
         }
     }
     if (!fail && !mbar_wait_bounded(&bar, phase & 1)) fail = 1;
-    tc_fence_after();
     __syncthreads();
     const bool ok = !fail;
-    // epilogue: TMEM -> shared staging [128][129] complex -> coalesced rows (and the mirror)
+    // after a timeout, give products still in flight one more bounded wait before TMEM is freed
+    if (!ok) mbar_wait_bounded(&bar, phase & 1);
+    tc_fence_after();
+    // epilogue in two passes of 64 columns: TMEM -> shared staging [128][65] -> coalesced rows (and
+    // the mirror)
     float2 *out = reinterpret_cast<float2 *>(sm);
-    if (ok) {
-        const int q = warp & 3, half_cols = warp >> 2;   // warps 0-3: columns 0-63, warps 4-7: 64-127
-        const int row = 32 * q + lane;
+    float2 *Cf = a.C + (long long)f * a.sCf;
+    const bool diag = RECIP && vb == rb;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (ok) {
+            const int q = warp & 3, hc = warp >> 2;   // lanes 32q.., columns 32hc.. of this pass
+            const int row = 32 * q + lane;
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            const int col = 64 * half_cols + c0;
-            float re[16], im[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col, re);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128 + col, im);
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                const int col = 64 * pass + 32 * hc + c0;
+                float re[16], im[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col, re);
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128 + col, im);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) out[row * 129 + col + j] = make_float2(re[j] * a.outscale, im[j] * a.outscale);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (ok) {
-        float2 *Cf = a.C + (long long)f * a.sCf;
-        const bool diag = RECIP && vb == rb;
-        for (int e = tid; e < 128 * 128; e += TC_THREADS) {
-            const int row = e >> 7, col = e & 127, v = v0 + row, r = r0 + col;
-            if (v < a.nv && r < a.nr && (!diag || v <= r)) Cf[(long long)v * a.ldr + r] = out[row * 129 + col];
-        }
-        if (RECIP) {
-            for (int e = tid; e < 128 * 128; e += TC_THREADS) {
-                const int rr = e >> 7, vv = e & 127, v = v0 + vv, r = r0 + rr;
-                if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = out[vv * 129 + rr];
+                for (int j = 0; j < 16; ++j)
+                    out[row * 65 + 32 * hc + c0 + j] = make_float2(re[j] * a.outscale, im[j] * a.outscale);
             }
         }
-    } else if (tid == 0) {
-        atomicOr(a.status, 2);
+        tc_fence_before();
+        __syncthreads();
+        if (ok) {
+            const int rp = r0 + 64 * pass;
+            for (int e = tid; e < 128 * 64; e += TC_THREADS) {
+                const int row = e >> 6, col = e & 63, v = v0 + row, r = rp + col;
+                if (v < a.nv && r < a.nr && (!diag || v <= r)) Cf[(long long)v * a.ldr + r] = out[row * 65 + col];
+            }
+            if (RECIP) {
+                for (int e = tid; e < 128 * 64; e += TC_THREADS) {
+                    const int rr = e >> 7, vv = e & 127, v = v0 + vv, r = rp + rr;
+                    if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = out[vv * 65 + rr];
+                }
+            }
+        }
+        __syncthreads();
     }
-    if (warp == 0) tmem_dealloc(tmem, TcAdj::TMEM_COLS);
+    if (!ok && tid == 0) atomicOr(a.status, 2);
+    if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -167,8 +167,11 @@ __host__ __device__ constexpr int padi(int i) { return i + 2 * (i >> 4); }
 #ifndef SMDD_FFT_MINB_LARGE          // the same for M >= 1024 (teams of 64 threads or more)
 #define SMDD_FFT_MINB_LARGE SMDD_FFT_MINB
 #endif
+#ifndef SMDD_FFT_MIN_TR              // fewest traces per CTA for M <= 1024
+#define SMDD_FFT_MIN_TR 2
+#endif
 #ifndef SMDD_FFT_NAMED_BAR           // 1: teams of more than one warp sync on their own named barrier
-#define SMDD_FFT_NAMED_BAR 0
+#define SMDD_FFT_NAMED_BAR 1
 #endif
 
 template <int M>
@@ -176,7 +179,13 @@ struct Team {
     static constexpr int P = FFT_P;
     static constexpr int T = M / P;                           // threads per trace
     static constexpr int TR_RAW = SMDD_FFT_TRACES * 512 / M;  // SMDD_FFT_TRACES traces per CTA at M = 512
-    static constexpr int TR = TR_RAW < 2 ? 2 : (T * TR_RAW > 1024 ? 1024 / T : TR_RAW);   // traces per CTA
+    // traces per CTA: a CTA moves TR consecutive traces x 8 bytes of each frequency row of the
+    // spectra, so small TR wastes sectors; at M = 2048 the CTA takes as many traces as 1024 threads
+    // hold (8: 64-byte rows; measured 1.5x faster than 2 traces despite 64 registers per thread), else
+    // at least SMDD_FFT_MIN_TR; at most 1024 threads
+    static constexpr int TR_MIN = M == 2048 ? 1024 / T : SMDD_FFT_MIN_TR;
+    static constexpr int TR_LO = TR_RAW < TR_MIN ? TR_MIN : TR_RAW;
+    static constexpr int TR = T * TR_LO > 1024 ? 1024 / T : TR_LO;
     static constexpr int THREADS = T * TR;                    // CTA size
     // float2 per trace buffer: padi(M) is a multiple of 16; the extra 16/TR float2 make the TR traces x
     // 16/TR bins that a half-warp touches in the tile loads / stores fall on 16 distinct bank pairs

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/smdd.h"
@@ -60,7 +61,18 @@ struct GemmArgs {
     float outscale;
     int tiles_v, tiles_r;    // adjoint tile grid
     int *status;
+    int nf_active;           // band limit: bins f >= nf_active (when > 0) get zero products
 };
+
+// Zero the output tile [r0, r0+nrows) x [c0, c0+ncols) of a CTA whose frequency bin lies above the
+// band limit (inside the matrix bounds rmax x cmax; leading dimension ld).
+__device__ __forceinline__ void zero_tile(float2 *C, long long ld, int r0, int nrows, int c0, int ncols, int rmax,
+                                          int cmax) {
+    for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
+        const int i = e / ncols, j = e % ncols, r = r0 + i, c = c0 + j;
+        if (r < rmax && c < cmax) C[(long long)r * ld + c] = make_float2(0.f, 0.f);
+    }
+}
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st);
@@ -90,6 +102,23 @@ struct PlanShape {
 PlanShape plan_shape(const mdc_plan_s *p);
 bool plan_begin_capture(mdc_plan_s *p);               // returns the profiling flag it switched off
 void plan_end_capture(mdc_plan_s *p, bool profiling);
+
+// LSQR workspace (owned by a plan, allocated on first use) and the iteration (lsqr.cu)
+struct LsqrWork {
+    float *u = nullptr, *t = nullptr;           // data-size vectors [ns][nv][nt]
+    float *v = nullptr, *w = nullptr, *g = nullptr;   // model-size vectors [nv][nr][nt]
+    int32_t *idx = nullptr;                     // 0 .. ns-1
+    double *partials = nullptr;
+    void *scalars = nullptr;
+    long long nd = 0, nm = 0;
+    cudaError_t ensure(long long n_data, long long n_model, int ns);
+    void release();
+    ~LsqrWork();
+};
+using OperatorFn = std::function<cudaError_t(const float *, float *)>;
+cudaError_t lsqr_run(LsqrWork &wk, float *x, const float *b, long long nd, long long nm, int nt, int n_iter,
+                     const int32_t *mute, double *norms, cudaStream_t st, const OperatorFn &apply_fwd,
+                     const OperatorFn &apply_adj, long long *launches);
 
 cudaError_t launch_power_iter(const float2 *Dh, int ns, int nr, int ldr, long long sDf, int nf, int n_iter,
                               double *lam, cudaStream_t st);

@@ -428,3 +428,30 @@ def test_lsqr_on_mdc_reaches_least_squares_and_keeps_preconditioned_range():
     assert all(b <= a * (1 + 1e-12) for a, b in zip(norms, norms[1:]))     # monotone residual estimates
     Xr, _ = oracle.mdc_lsqr(D, np.zeros((n, n, nt)), U, 6, recip=True)
     np.testing.assert_allclose(Xr, np.transpose(Xr, (1, 0, 2)), rtol=0, atol=1e-12)
+
+
+def test_band_limited_operator_is_direct_sums_with_lowpassed_kernel():
+    """Zeroing the products above bin `band` equals the direct sums (Tier A) with the down-going field
+    passed through the ideal low-pass filter of the same FFT length (a separate route to the same operator)."""
+    nt, nr, nv, ns, band = 40, 4, 3, 5, 17
+    D = synth.random_traces((ns, nr, nt), 91)
+    X = synth.random_traces((nv, nr, nt), 92)
+    R = synth.random_traces((3, nv, nt), 93)
+    idx = np.array([4, 0, 2])
+    nfft = oracle.default_nfft(nt)
+    Dh = np.fft.rfft(D, n=nfft, axis=-1)
+    Dh[..., band:] = 0.0
+    Dlp = np.fft.irfft(Dh, n=nfft, axis=-1)          # the filtered kernel, full length nfft
+    # direct sums with a kernel of length nfft: the causal sum only needs tau < nt, but the filtered
+    # kernel is not causal-limited, so wrap the tail (tau in [nt, nfft)) as the circular product does
+    U = np.zeros((3, nv, nt))
+    G = np.zeros((nv, nr, nt))
+    for b, s in enumerate(idx):
+        for v in range(nv):
+            for r in range(nr):
+                for t in range(nt):
+                    U[b, v, t] += sum(Dlp[s, r, (t - k) % nfft] * X[v, r, k] for k in range(nt))
+                    G[v, r, t] += sum(Dlp[s, r, (k - t) % nfft] * R[b, v, k] for k in range(nt))
+    np.testing.assert_allclose(oracle.mdc_forward_fft(D, X, idx, band=band), U, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(oracle.mdc_adjoint_fft(D, R, idx, band=band), G, rtol=1e-10, atol=1e-10)
+    np.testing.assert_array_equal(oracle.mdc_forward_fft(D, X, idx, band=nfft // 2 + 1), oracle.mdc_forward_fft(D, X, idx))
