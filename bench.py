@@ -132,6 +132,24 @@ def ncu_traffic(stage: str, workload: str):
 
 
 # ------------------------------------------------------------------------------------------------
+# combining the ranks (one independent replica per GPU)
+# ------------------------------------------------------------------------------------------------
+def combine_ranks(times, flops: float, device=None):
+    """Max over ranks of each time and sum over ranks of the flops (all ranks call it; a no-op without
+    an initialised process group of more than one rank).  Returns (times, flops)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(times), float(flops)
+    tt = torch.tensor(list(times), dtype=torch.float64, device=device)
+    ff = torch.tensor([float(flops)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ff, op=dist.ReduceOp.SUM)
+    return tt.tolist(), ff.item()
+
+
+# ------------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------------
 class ClockSampler:
@@ -199,9 +217,8 @@ def make_inputs(w, seed):
 
 def workload_dims(name):
     w = dict(synth.WORKLOADS[name])
-    nums = {"smdd_nt128_n32_nb8": (32, 32, 32), "smdd_nt512_n201_nb16_recip": (201, 201, 201),
-            "smdd_nt512_n256_nb16_recip": (256, 256, 256), "smdd_nt1024_n301_ns401_nb32": (301, 301, 401)}
-    w["nr"], w["nv"], w["ns"] = nums[name]
+    for k in ("nr", "nv", "ns"):
+        w.setdefault(k, w.get("n"))
     return w
 
 
@@ -237,6 +254,39 @@ def time_oracle(w, D, X, U_obs, batches, target_s=12.0, max_cols=None):
     sample = (f"forward+adjoint direct sums (FP64) for {k} of {nv} virtual-source columns of one batch of "
               f"{len(idx)} sources, extrapolated linearly in the column count ({t1 - t0:.1f} s measured)")
     return f / t_step / 1e9, t_step, sample, oracle.num_threads()
+
+
+def oracle_extra(w, D, X, U_obs, idx, target_s=3.0):
+    """The oracle's other timings for one step: the direct sums on one thread, and the FP64 FFT tier
+    (numpy) -- each on a column sample of about target_s, extrapolated in the column count."""
+    import oracle
+    nv = w["nv"]
+    cores = oracle.num_threads()
+    res = {}
+    try:
+        oracle.set_num_threads(1)
+        t0 = time.perf_counter()
+        oracle_step_sample(D, X, U_obs, idx, np.arange(1))
+        per_col = max(time.perf_counter() - t0, 1e-6)
+        k = int(min(nv, max(1, target_s / per_col)))
+        vsel = np.linspace(0, nv - 1, k).round().astype(np.int64)
+        t0 = time.perf_counter()
+        oracle_step_sample(D, X, U_obs, idx, vsel)
+        t1 = (time.perf_counter() - t0) * nv / k
+    finally:
+        oracle.set_num_threads(cores)
+    macs = 2.0 * len(idx) * w["nv"] * w["nr"] * w["nt"] * (w["nt"] + 1) / 2   # forward + adjoint direct sums
+    res["tier_a_1thread_s_per_step"] = round(t1, 3)
+    res["tier_a_1thread_gflops"] = round(step_flops(w["nt"], w["nr"], w["nv"], len(idx)) / t1 / 1e9, 5)
+    res["tier_a_1thread_direct_mac_per_s"] = round(macs / t1, 1)
+    t0 = time.perf_counter()
+    k = max(1, min(nv, 4))
+    vsel = np.arange(k)
+    Uf = oracle.mdc_forward_fft(D, X[vsel], idx)
+    oracle.mdc_adjoint_fft(D, Uf - U_obs[idx][:, vsel], idx)
+    res["tier_b_fft_s_per_step"] = round((time.perf_counter() - t0) * nv / k, 3)
+    res["tier_b_sample"] = f"{k} of {nv} virtual-source columns, extrapolated"
+    return res
 
 
 # ------------------------------------------------------------------------------------------------
@@ -369,13 +419,7 @@ def run_gpu(args, rank, world, w):
     t_e2e = time.perf_counter() - e0
 
     # max over ranks
-    tt = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device=dev)
-    ff = torch.tensor([flops], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(ff, op=torch.distributed.ReduceOp.SUM)
-    t_dev, t_e2e, wall = tt.tolist()
-    flops_all = ff.item()
+    (t_dev, t_e2e, wall), flops_all = combine_ranks([t_dev, t_e2e, wall], flops, dev)
     if rank != 0:
         return None
 
@@ -442,8 +486,11 @@ def run_gpu(args, rank, world, w):
         Xs = np.zeros((nv, nr, nt))
         Uo = U_obs.double().cpu().numpy()
         val, t_step, sample, cores = time_oracle(w, D64, Xs, Uo, [batches[args.warmup:]])
+        macs = 2.0 * nb * nv * nr * nt * (nt + 1) / 2
         out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample, "s_per_step_extrapolated": round(t_step, 3)}
+                               "sample": sample, "s_per_step_extrapolated": round(t_step, 3),
+                               "steps_per_s": round(1.0 / t_step, 5), "direct_mac_per_s": round(macs / t_step, 1)}
+        out["cpu_baseline"].update(oracle_extra(w, D64, Xs, Uo, batches[args.warmup]))
     return out
 
 
@@ -631,12 +678,7 @@ def run_gpu_batch(args, rank, world):
     roof["member"] = {k: sb[k] for k in ("nt", "nr", "nv", "ns", "nb")}
     roof["stage_ms_per_launch"] = {k: round(v[0] / v[1], 4) for k, v in st.items()}
 
-    tt = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device=dev)
-    ff = torch.tensor([epoch_flops * args.steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(ff, op=torch.distributed.ReduceOp.SUM)
-    t_dev, t_e2e, wall = tt.tolist()
+    (t_dev, t_e2e, wall), flops_all = combine_ranks([t_dev, t_e2e, wall], epoch_flops * args.steps, dev)
     if rank != 0:
         return None
     cfgs = {}
@@ -644,7 +686,7 @@ def run_gpu_batch(args, rank, world):
         key = f"fft{sp['cfg']['fft_variant']}_fwd{sp['cfg']['gemm_fwd']}_adj{sp['cfg']['gemm_adj']}"
         cfgs[key] = cfgs.get(key, 0) + 1
     out = {
-        "metric": METRIC, "value": round(ff.item() / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": round(flops_all / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_dev / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
@@ -656,7 +698,7 @@ def run_gpu_batch(args, rank, world):
                    "autotuned": bool(args.autotune), "chosen_configs": cfgs,
                    "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1),
                    "per_rank": "independent member set, seeds offset by rank (no data-path collective)"},
-        "e2e": {"value": round(ff.item() / t_e2e / 1e9, 2), "unit": UNIT,
+        "e2e": {"value": round(flops_all / t_e2e / 1e9, 2), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches) * world,
         "roofline": roof,

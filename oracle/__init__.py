@@ -57,6 +57,8 @@ def _load():
             fn.argtypes = [ctypes.c_int] * 4 + [dp, dp, ip, ctypes.c_int, ip, ctypes.c_int,
                                                 ctypes.c_double, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = None
         _lib = lib
     return _lib
 
@@ -64,6 +66,11 @@ def _load():
 def num_threads() -> int:
     """OpenMP threads the direct sums use."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Set the OpenMP threads of the direct sums (timing only; the results do not depend on it)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def _f64(a):
