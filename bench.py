@@ -318,7 +318,7 @@ def run_gpu(args, rank, world, w):
         rms = U_obs.pow(2).mean().sqrt()
         U_obs += w["noise"] * rms * torch.from_numpy(p.noise.astype(np.float32)).to(dev)
     gen.close()
-    if args.fixed_error_epochs <= 0:
+    if args.fixed_error_epochs <= 0 and args.solver_epochs <= 0:
         del X_true
 
     prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
@@ -481,6 +481,8 @@ def run_gpu(args, rank, world, w):
     }
     if args.fixed_error_epochs > 0:
         out["fixed_error"] = precision_comparison(args, dev, D, U_obs, X_true, w, rank)
+    if args.solver_epochs > 0:
+        out["solvers"] = solver_comparison(args, dev, D, U_obs, X_true, w, rank)
     if world == 1 or rank == 0:
         D64 = p.D.astype(np.float32).astype(np.float64)
         Xs = np.zeros((nv, nr, nt))
@@ -542,6 +544,74 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
     res["definition"] = ("same batches from X = 0; model error = ||X - X_true|| / ||X_true||; BF16x3 runs until "
                          "its error is within 0.1% of the FP32 error after the FP32 epochs (the two differ by "
                          "rounding only); device time of the steps")
+    return res
+
+
+def solver_comparison(args, dev, D, U_obs, X_true, w, rank):
+    """The paper's comparison of solvers on the same problem, in epochs (one epoch = every source once:
+    ceil(ns/nb) stochastic steps, or one full-gradient LSQR iteration): SGD (alpha = 0.5 * 2/sigma^2),
+    N-SGD (mu = 0.9, alpha = 0.25 * 2/sigma^2) and LSQR, all with the workload's reciprocity flag, from
+    X = 0.  Reports the model error ||X - X_true|| / ||X_true|| after every epoch, the device time, and the
+    epochs each solver needs to reach SGD's final error."""
+    import torch
+
+    from paper_2202_04486_gb300 import binding
+
+    nt, nr, nv, ns, nb = w["nt"], w["nr"], w["nv"], w["ns"], w["nb"]
+    recip = bool(w["reciprocity"])
+    n_ep = args.solver_epochs
+    batches = synth.epoch_batches(ns, nb, n_ep, seed=200 + rank)
+    idx_dev = [[torch.from_numpy(b).to(dev) for b in ep] for ep in batches]
+    xt = X_true.double()
+    xt_norm = xt.norm().item()
+    rflag = binding.SMDD_RECIPROCITY if recip else 0
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for solver in ("sgd", "nsgd", "lsqr"):
+        plan = binding.MDCPlan(D, nv, nb_max=ns if solver == "lsqr" else nb)
+        sigma2 = plan.sigma2_max(60)
+        X = torch.zeros((nv, nr, nt), device=dev)
+        V = torch.zeros_like(X)
+        errs, t = [], 0.0
+        if solver == "lsqr":
+            # LSQR cannot be resumed from its iterate alone: each checkpoint count runs from zero
+            checks = sorted({k for k in (1, 2, 3, 5, 10, 20, 30, 50, 100, 200) if k < n_ep} | {n_ep})
+            for k in checks:
+                X.zero_()
+                e0.record()
+                binding.smdd_lsqr(plan.handle, X, U_obs, k, rflag)
+                e1.record()
+                torch.cuda.synchronize()
+                if k == n_ep:
+                    t = e0.elapsed_time(e1) / 1e3
+                errs.append((k, (X.double() - xt).norm().item() / xt_norm))
+        else:
+            alpha = (0.5 if solver == "sgd" else 0.25) * 2.0 / sigma2
+            k = 0
+            for ep in idx_dev:
+                e0.record()
+                for ii in ep:
+                    fl = rflag | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+                    if solver == "sgd":
+                        binding.smdd_step(plan.handle, X, U_obs, ii, alpha, fl)
+                    else:
+                        binding.smdd_step_ex(plan.handle, X, U_obs, ii, alpha, fl | binding.SMDD_NESTEROV, V=V, mu=0.9)
+                    k += 1
+                e1.record()
+                torch.cuda.synchronize()
+                t += e0.elapsed_time(e1) / 1e3
+                errs.append((len(errs) + 1, (X.double() - xt).norm().item() / xt_norm))
+        if plan.sync_status() != binding.MDC_OK:
+            raise RuntimeError(f"device status after {solver}")
+        res[solver] = {"model_error_at_epoch": {k: round(e, 5) for k, e in errs}, "device_s": round(t, 4)}
+        plan.close()
+    target = res["sgd"]["model_error_at_epoch"][n_ep]
+    for solver in ("sgd", "nsgd", "lsqr"):
+        errs = res[solver]["model_error_at_epoch"]
+        res[solver]["epochs_to_sgd_final_error"] = next((k for k in sorted(errs) if errs[k] <= target), None)
+    res["definition"] = ("model error = ||X - X_true|| / ||X_true|| after each epoch; an epoch is ceil(ns/nb) "
+                         "stochastic steps or one LSQR iteration (every source once); LSQR is evaluated at "
+                         f"checkpoint iteration counts, each run from zero; LSQR device_s is for {n_ep} iterations")
     return res
 
 
@@ -783,6 +853,8 @@ def main():
     ap.add_argument("--batch-largest", type=int, default=1,
                     help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")
     ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
+    ap.add_argument("--solver-epochs", type=int, default=0,
+                    help="also compare SGD, N-SGD and full-gradient LSQR over this many epochs (model error per epoch)")
     ap.add_argument("--fixed-error-epochs", type=int, default=0,
                     help="also compare FP32 and BF16x3 products at the same final-model error after this many epochs")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"],
