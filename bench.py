@@ -239,7 +239,7 @@ def time_oracle(w, D, X, U_obs, batches, target_s=12.0, max_cols=None):
     import oracle
     nv = w["nv"]
     idx = batches[0][0]
-    cols = 2
+    cols = min(2, nv)
     t0 = time.perf_counter()
     oracle_step_sample(D, X, U_obs, idx, np.arange(cols))
     t1 = time.perf_counter()

@@ -200,7 +200,10 @@ int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float 
 
 typedef struct {
     int fft_variant;   /* 0: default radix order of the FFT plan; 1: the reversed order (accepted for
-                          every size, identical to 0 where all radices are equal) */
+                          every size, identical to 0 where all radices are equal); 2: the two-pass FFT
+                          (32 values per thread, one shared-memory exchange per transform; FFT lengths
+                          256 .. 2048, i.e. nfft/2 in 128 .. 1024; elsewhere 2 means 0).  Steps with
+                          N-SGD or the causality mute run variant 0 whatever is set. */
     int gemm_fwd;      /* MDC_GEMM_SIMT or MDC_GEMM_TC */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
     int reserved[5];   /* zero */

@@ -44,8 +44,8 @@ struct mdc_plan_s {
     float2 *Dh = nullptr;        // [nf][ns][ldr]
     float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
     float2 *Uh = nullptr;        // [nf][nv][ldb]  batch spectra (prediction, then residual)
-    float2 *tw = nullptr;        // per-pass twiddle tables of both radix-order variants (variant 1 at tw1_off)
-    int tw1_off = 0;
+    float2 *tw = nullptr;        // twiddle tables of the FFT variants: 0 at 0, 1 at tw1_off, 2 at tw2_off
+    int tw1_off = 0, tw2_off = 0;
     float2 *twN = nullptr;       // [M+1]
     double *partials = nullptr;  // residual-kernel block partials
     double *lam = nullptr;       // [nf] power-iteration results, [nf] = max
@@ -106,7 +106,7 @@ FftArgs base_fft(const mdc_plan_s *p) {
     FftArgs a;
     memset(&a, 0, sizeof(a));
     a.nt = p->nt;
-    a.tw = p->tw + (p->fft_variant ? p->tw1_off : 0);
+    a.tw = p->tw + (p->fft_variant == 2 ? p->tw2_off : p->fft_variant == 1 ? p->tw1_off : 0);
     a.variant = p->fft_variant;
     a.twN = p->twN;
     a.s = p->scale / (float)p->nfft;
@@ -125,12 +125,16 @@ int ti_log2_for(int n_contig, int TR) {
 // time traces may be read and written as float4: every trace starts on a 16-byte boundary
 bool vec4_ok(int nt, const void *p) { return nt % 4 == 0 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+int traces_per_cta(const mdc_plan_s *p) {
+    return p->fft_variant == 2 ? fft2_traces_per_cta(p->M) : fft_traces_per_cta(p->M);
+}
+
 // model-layout grid: trace (i = r, j = v) of a [nv][nr][nt] array  <->  spectra [nf][nv][ldr]
 TraceGrid model_grid(const mdc_plan_s *p, int nouter) {
     TraceGrid g;
     g.ni = p->nr;
     g.nj = nouter;
-    g.ti_log2 = ti_log2_for(p->nr, fft_traces_per_cta(p->M));
+    g.ti_log2 = ti_log2_for(p->nr, traces_per_cta(p));
     g.tsi = p->nt;
     g.tsj = (long long)p->nr * p->nt;
     g.ssi = 1;
@@ -144,7 +148,7 @@ TraceGrid batch_grid(const mdc_plan_s *p, int nb) {
     TraceGrid g;
     g.ni = nb;
     g.nj = p->nv;
-    g.ti_log2 = ti_log2_for(nb, fft_traces_per_cta(p->M));
+    g.ti_log2 = ti_log2_for(nb, traces_per_cta(p));
     g.tsi = (long long)p->nv * p->nt;
     g.tsj = p->nt;
     g.ssi = 1;
@@ -318,6 +322,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     p->prec = precision;
     p->gemm_fwd = p->gemm_adj = (precision == MDC_PREC_BF16X3) ? MDC_GEMM_TC : MDC_GEMM_SIMT;
     p->tw1_off = ((fft_tw_size(nfft / 2, 0) > 1 ? fft_tw_size(nfft / 2, 0) : 1) + 1) & ~1;
+    p->tw2_off = p->tw1_off + (((fft_tw_size(nfft / 2, 1) > 1 ? fft_tw_size(nfft / 2, 1) : 1) + 1) & ~1);
 
     const int M = p->M, nf = p->nf;
     const size_t szD = (size_t)nf * ns * p->ldr * sizeof(float2);
@@ -326,9 +331,15 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     {
         TraceGrid g = batch_grid(p, nb_max);
         p->resid_blocks_max = fft_blocks(M, g);
+        if (fft2_supported(M)) {   // the residual kernel of every FFT variant fits the partials buffer
+            p->fft_variant = 2;
+            TraceGrid g2 = batch_grid(p, nb_max);
+            p->resid_blocks_max = std::max(p->resid_blocks_max, fft2_blocks(M, g2));
+            p->fft_variant = 0;
+        }
     }
     bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
-              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw1_off + fft_tw_size(M, 1) + 1) * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw2_off + M + 2) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->twN, (M + 1) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->partials, (size_t)(p->resid_blocks_max + 1) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&p->lam, (size_t)(nf + 1) * sizeof(double)) == cudaSuccess &&
@@ -348,6 +359,12 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     if (cudaMemcpyAsync(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = MDC_ERR_CUDA;
     if (cudaMemcpyAsync(p->tw + p->tw1_off, tw1.data(), tw1.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = MDC_ERR_CUDA;
+    std::vector<float2> tw2;
+    if (fft2_supported(M)) {
+        fft2_tw_fill(M, tw2);
+        if (cudaMemcpyAsync(p->tw + p->tw2_off, tw2.data(), tw2.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = MDC_ERR_CUDA;
+    }
     std::vector<float2> twn(M + 1);
     for (int k = 0; k <= M; ++k) {
         const double ang = 2.0 * pi * (double)k / (double)nfft;
@@ -604,7 +621,7 @@ int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
     if (!p || !cfg) return MDC_ERR_INVALID_ARG;
     for (int i = 0; i < 5; ++i)
         if (cfg->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
-    if (cfg->fft_variant != 0 && cfg->fft_variant != 1) return MDC_ERR_INVALID_ARG;
+    if (cfg->fft_variant < 0 || cfg->fft_variant > 2) return MDC_ERR_INVALID_ARG;
     if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
     if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
     if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_adj == MDC_GEMM_TC) && p->prec != MDC_PREC_BF16X3)
@@ -667,7 +684,7 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     if (rc == MDC_OK) {
         // FFT radix order, on the fused update (inverse + forward transform of every trace)
         double tbest = 1e300;
-        for (int v = 0; v < 2 && rc == MDC_OK; ++v) {
+        for (int v = 0; v < 3 && rc == MDC_OK; ++v) {
             if (!fft_has_variant(p->M, v)) continue;
             p->fft_variant = v;
             const double t = time_it([&] {

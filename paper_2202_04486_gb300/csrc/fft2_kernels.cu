@@ -1,0 +1,362 @@
+// The trace kernels of fft_kernels.cu (rfft, irfft with window, residual step, update step) on the
+// two-pass FFT of smdd_fft2.cuh (radix-order variant 2, 128 <= M <= 1024).  Same arguments, same
+// results; a team of M/32 threads per trace, 32 values per thread, one shared-memory exchange per
+// transform, the real-signal post-processing through warp shuffles.
+//
+// Time samples: thread t of a team holds z[n] = (x[2n], x[2n+1]) for n = t + T m, so for every m the
+// team reads / writes 2T consecutive samples.
+#include <cmath>
+#include <vector>
+
+#include "smdd_fft2.cuh"
+#include "smdd_internal.h"
+
+namespace smdd {
+
+namespace {
+
+struct TileCoord2 {
+    int i, j;
+    bool valid;
+};
+
+template <int M>
+__device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr) {
+    constexpr int TR = Fft2<M>::TR;
+    const int ti = 1 << g.ti_log2;
+    const int tj = TR >> g.ti_log2;
+    const int ntile_i = (g.ni + ti - 1) / ti;
+    const int bi = blockIdx.x % ntile_i, bj = blockIdx.x / ntile_i;
+    TileCoord2 c;
+    c.i = bi * ti + (tr & (ti - 1));
+    c.j = bj * tj + (tr >> g.ti_log2);
+    c.valid = c.i < g.ni && c.j < g.nj;
+    return c;
+}
+
+// spectra of the CTA's traces -> shared memory (slot 0 = (Re X[0], Re X[M])); thread binding: trace
+// tr = tid % TR, bins f = tid / TR + it * (THREADS / TR)
+template <int M>
+__device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g) {
+    using F = Fft2<M>;
+    constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord2 c = coord2_of<M>(g, tr);
+    float2 v[NIT];
+    float nyq = 0.f;
+    if (c.valid) {
+        const float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) v[it] = __ldcs(s + (long long)(f0 + it * STEP) * g.ssf);
+        if (f0 == 0) nyq = __ldcs(s + (long long)M * g.ssf).x;
+    } else {
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) v[it] = make_float2(0.f, 0.f);
+    }
+    float2 *b = sm + tr * STR;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int f = f0 + it * STEP;
+        b[pad2(f)] = (f == 0) ? make_float2(v[it].x, nyq) : v[it];
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void tile2_store(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g) {
+    using F = Fft2<M>;
+    constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord2 c = coord2_of<M>(g, tr);
+    if (!c.valid) return;
+    const float2 *b = sm + tr * STR;
+    float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int f = f0 + it * STEP;
+        const float2 v = b[pad2(f)];
+        s[(long long)f * g.ssf] = (f == 0) ? make_float2(v.x, 0.f) : v;
+    }
+    if (f0 == 0) s[(long long)M * g.ssf] = make_float2(b[0].y, 0.f);
+}
+
+// the two samples of element n (window [0, nt)); vec: the trace may be read as float2
+__device__ __forceinline__ float2 load_z(const float *x, int n, int nt, bool vec) {
+    const int i0 = 2 * n;
+    if (vec && i0 + 1 < nt) return __ldcs(reinterpret_cast<const float2 *>(x + i0));
+    float2 z = make_float2(0.f, 0.f);
+    if (i0 < nt) z.x = x[i0];
+    if (i0 + 1 < nt) z.y = x[i0 + 1];
+    return z;
+}
+__device__ __forceinline__ void store_z(float *y, int n, int nt, bool vec, float2 z) {
+    const int i0 = 2 * n;
+    if (vec && i0 + 1 < nt) {
+        *reinterpret_cast<float2 *>(y + i0) = z;
+    } else {
+        if (i0 < nt) y[i0] = z.x;
+        if (i0 + 1 < nt) y[i0 + 1] = z.y;
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_rfft(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    using F = Fft2<M>;
+    constexpr int T = F::T;
+    const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    float2 *buf = sm + tr * F::STRIDE;
+    const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
+    float2 v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = (m < 16 && c.valid) ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    __syncthreads();
+    tile2_store<M>(sm, a.spec, a.g);
+}
+
+template <int M>
+__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_irfft_out(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    using F = Fft2<M>;
+    constexpr int T = F::T;
+    const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    tile2_load<M>(sm, a.spec, a.g);
+    __syncthreads();
+    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    float2 *buf = sm + tr * F::STRIDE;
+    float2 v[32];
+    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    if (!c.valid) return;   // no barrier follows
+    float *y = a.tout + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) store_z(y, t + T * m, a.nt, a.vec, make_float2(v[m].x * a.s, v[m].y * a.s));
+}
+
+__device__ __forceinline__ double block_sum2(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();   // red may still be read by a previous call
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
+    return s;   // valid in thread 0
+}
+
+// residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], FP64 loss partials, Rh = rfft(R) in place
+template <int M>
+__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_residual(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    using F = Fft2<M>;
+    constexpr int T = F::T;
+    const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    const float *uo = nullptr;
+    if (c.valid) {
+        int row = c.i;
+        if (!a.gathered) {
+            row = a.idx[c.i];
+            if (row < 0 || row >= a.ns) {
+                atomicOr(a.status, 1);
+                row = -1;
+            }
+        }
+        if (row >= 0) uo = a.uobs + (long long)row * a.uo_si + (long long)c.j * a.uo_sj;
+    }
+    float2 o[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) o[m] = uo ? load_z(uo, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    tile2_load<M>(sm, a.spec, a.g);
+    __syncthreads();
+    float2 *buf = sm + tr * F::STRIDE;
+    float2 v[32];
+    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    double l2 = 0.0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        if (m < 16) {
+            const int i0 = 2 * (t + T * m);
+            float2 q = make_float2(0.f, 0.f);
+            if (c.valid) {
+                q.x = (i0 < a.nt) ? fmaf(v[m].x, a.s, -o[m].x) : 0.f;
+                q.y = (i0 + 1 < a.nt) ? fmaf(v[m].y, a.s, -o[m].y) : 0.f;
+                l2 += (double)q.x * q.x + (double)q.y * q.y;
+            }
+            v[m] = q;
+        } else {
+            v[m] = make_float2(0.f, 0.f);
+        }
+    }
+    rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    __syncthreads();
+    tile2_store<M>(sm, a.spec, a.g);
+
+    const double bs = block_sum2(l2, red);
+    if (threadIdx.x == 0) {
+        const int nblk = gridDim.x;
+        a.partials[blockIdx.x] = bs;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.counter, 1u);
+        am_last = (prev == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (am_last) {   // block-uniform
+        __threadfence();
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&a.partials[b]);
+        s = block_sum2(s, red);   // fixed assignment and order: deterministic
+        if (threadIdx.x == 0) {
+            if (a.loss) *a.loss = 0.5 * s;
+            *a.counter = 0u;
+        }
+    }
+}
+
+// update step: g = s * irfft(Gh)[0:nt]; X <- X - alpha g; optionally Gh <- rfft(X_new) in place
+template <int M, bool KEEP>
+__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_update(FftArgs a) {
+    extern __shared__ __align__(16) float2 sm[];
+    using F = Fft2<M>;
+    constexpr int T = F::T;
+    const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
+    float2 xo[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) xo[m] = c.valid ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    tile2_load<M>(sm, a.spec, a.g);
+    __syncthreads();
+    float2 *buf = sm + tr * F::STRIDE;
+    float2 v[32];
+    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    const float nas = -a.alpha * a.s;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        if (m < 16) {
+            const int n = t + T * m, i0 = 2 * n;
+            float2 z;
+            z.x = (i0 < a.nt) ? fmaf(nas, v[m].x, xo[m].x) : 0.f;
+            z.y = (i0 + 1 < a.nt) ? fmaf(nas, v[m].y, xo[m].y) : 0.f;
+            if (c.valid) store_z(x, n, a.nt, a.vec, z);
+            v[m] = z;
+        } else {
+            v[m] = make_float2(0.f, 0.f);
+        }
+    }
+    if constexpr (KEEP) {
+        rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+        __syncthreads();
+        tile2_store<M>(sm, a.spec, a.g);
+    }
+}
+
+template <int M>
+int blocks2_for(const TraceGrid &g) {
+    const int ti = 1 << g.ti_log2, tj = Fft2<M>::TR >> g.ti_log2;
+    return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
+}
+
+#define SMDD_SWITCH_M2(M_, ...)                                      \
+    switch (M_) {                                                    \
+        case 128: { constexpr int MM = 128; __VA_ARGS__; } break;    \
+        case 256: { constexpr int MM = 256; __VA_ARGS__; } break;    \
+        case 512: { constexpr int MM = 512; __VA_ARGS__; } break;    \
+        case 1024: { constexpr int MM = 1024; __VA_ARGS__; } break;  \
+        default: return cudaErrorInvalidValue;                       \
+    }
+
+}  // namespace
+
+bool fft2_supported(int M) { return M >= 128 && M <= 1024; }
+
+int fft2_traces_per_cta(int M) {
+    switch (M) {
+        case 128: return Fft2<128>::TR;
+        case 256: return Fft2<256>::TR;
+        case 512: return Fft2<512>::TR;
+        case 1024: return Fft2<1024>::TR;
+    }
+    return 0;
+}
+
+int fft2_blocks(int M, const TraceGrid &g) {
+    switch (M) {
+        case 128: return blocks2_for<128>(g);
+        case 256: return blocks2_for<256>(g);
+        case 512: return blocks2_for<512>(g);
+        case 1024: return blocks2_for<1024>(g);
+    }
+    return 0;
+}
+
+// pass-2 table [r][j'] = w_M^{r j'} (r < M/32, j' < 32), double precision rounded once
+void fft2_tw_fill(int M, std::vector<float2> &tw) {
+    const double pi = 3.14159265358979323846;
+    tw.assign(M, make_float2(0.f, 0.f));
+    for (int r = 0; r < M / 32; ++r)
+        for (int j = 0; j < 32; ++j) {
+            const double ang = 2.0 * pi * (double)(r * j) / (double)M;
+            tw[r * 32 + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+}
+
+template <int M>
+static cudaError_t prepare2_m() {
+    const int sm = (int)Fft2<M>::SMEM;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_rfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_irfft_out<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_residual<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_update<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_update<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
+cudaError_t fft2_prepare(int M) {
+    SMDD_SWITCH_M2(M, { return prepare2_m<MM>(); });
+    return cudaSuccess;
+}
+
+cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, {
+        const int nb = blocks2_for<MM>(a.g);
+        if (nb == 0) return cudaSuccess;
+        k2_rfft<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, {
+        const int nb = blocks2_for<MM>(a.g);
+        if (nb == 0) return cudaSuccess;
+        k2_irfft_out<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, {
+        const int nb = blocks2_for<MM>(a.g);
+        if (nb == 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
+        k2_residual<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch2_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, {
+        const int nb = blocks2_for<MM>(a.g);
+        if (nb == 0) return cudaSuccess;
+        if (keep) k2_update<MM, true><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+        else k2_update<MM, false><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+}  // namespace smdd

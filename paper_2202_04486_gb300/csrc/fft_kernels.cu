@@ -440,7 +440,9 @@ int fft_tw_size(int M, int v) {
     return 0;
 }
 
-bool fft_has_variant(int M, int v) { return v == 0 || (v == 1 && fft_variant_distinct(M)); }
+bool fft_has_variant(int M, int v) {
+    return v == 0 || (v == 1 && fft_variant_distinct(M)) || (v == 2 && fft2_supported(M));
+}
 
 void fft_tw_fill(int M, std::vector<float2> &tw, int v) {
     const double pi = 3.14159265358979323846;
@@ -486,11 +488,16 @@ static cudaError_t prepare_m() {
 }
 
 cudaError_t fft_prepare(int M) {
+    if (fft2_supported(M)) {
+        const cudaError_t e = fft2_prepare(M);
+        if (e != cudaSuccess) return e;
+    }
     SMDD_SWITCH_M(M, { return prepare_m<MM>(); });
     return cudaSuccess;
 }
 
 cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st) {
+    if (a.variant == 2) return launch2_rfft(M, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
@@ -502,6 +509,7 @@ cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
+    if (a.variant == 2) return launch2_irfft_out(M, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
@@ -513,6 +521,7 @@ cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st) {
+    if (a.variant == 2) return launch2_residual(M, a, nblocks_expected, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
@@ -524,6 +533,7 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
 }
 
 cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
+    if (a.variant == 2 && !a.vel && !a.mute) return launch2_update(M, keep, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;

@@ -43,7 +43,7 @@ struct FftArgs {
     unsigned int *counter;
     double *loss;
     int *status;
-    int variant;             // radix-order variant of the FFT plan (0 or 1, see fft_radix)
+    int variant;             // FFT variant: 0 / 1 radix orders of fft_radix, 2 the two-pass FFT (smdd_fft2.cuh)
     // update: Nesterov velocity (null for SGD), momentum, causality mute (first kept sample per
     // model trace, [nv][nr]; null for none)
     float *vel;
@@ -85,6 +85,17 @@ cudaError_t fft_prepare(int M);                                // opt-in to the 
 int fft_tw_size(int M, int variant = 0);
 bool fft_has_variant(int M, int variant);                     // variant 1 exists where it differs from 0
 void fft_tw_fill(int M, std::vector<float2> &tw, int variant = 0);   // host: per-pass twiddle tables
+
+// two-pass FFT kernels (radix-order variant 2, 128 <= M <= 1024; fft2_kernels.cu)
+bool fft2_supported(int M);
+int fft2_traces_per_cta(int M);
+int fft2_blocks(int M, const TraceGrid &g);
+void fft2_tw_fill(int M, std::vector<float2> &tw);   // host: the pass-2 table, M entries
+cudaError_t fft2_prepare(int M);
+cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st);
+cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st);
+cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st);
+cudaError_t launch2_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
 
 cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, int tile = 0);

@@ -44,20 +44,24 @@ def _check(gpu, ref, what, rel=REL_L2, elem=ELEM):
     assert m <= elem, f"{what}: max elementwise error {m:.3e} of max|ref| > {elem:.1e}"
 
 
-# one shape per FFT length whose reversed radix order differs from the default (M = 32, 128, 256,
-# 1024, 2048), ragged sizes, and one with nt = 2 mod 4
+# every FFT length where the reversed radix order (variant 1) differs from the default (M = 32, 128,
+# 256, 1024, 2048) or the two-pass FFT (variant 2) exists (M = 128 .. 1024), ragged sizes, odd nt and
+# nt = 2 mod 4 (scalar time I/O)
 VARIANT_SHAPES = [
     (30, 7, 5, 9, 4),         # nfft 64
     (100, 37, 29, 41, 5),     # nfft 256
     (200, 12, 10, 14, 6),     # nfft 512
+    (257, 17, 19, 23, 17),    # nfft 1024, odd nt
     (600, 20, 20, 20, 4),     # nfft 2048
     (1500, 6, 5, 7, 3),       # nfft 4096
     (130, 9, 9, 12, 7),       # nfft 512, scalar time I/O
+    (1024, 33, 35, 40, 9),    # nfft 2048, nt = M: no zero padding inside the first half
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("shape", VARIANT_SHAPES, ids=lambda s: "x".join(map(str, s)))
-def test_reversed_radix_order_matches_oracle(shape):
+def test_fft_variants_match_oracle(shape, variant):
     nt, nr, nv, ns, nb = shape
     seed = sum(shape)
     D = _f32(synth.random_traces((ns, nr, nt), seed))
@@ -65,12 +69,15 @@ def test_reversed_radix_order_matches_oracle(shape):
     R = _f32(synth.random_traces((nb, nv, nt), seed + 2))
     idx = synth.random_indices(ns, nb, seed + 3)
     plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, scale=0.5)
-    plan.set_config(fft_variant=1)
-    assert plan.get_config()["fft_variant"] == 1
+    plan.set_config(fft_variant=variant)
+    M = plan.nfft // 2
+    # variant 1 falls back to 0 where both radix orders coincide; variant 2 exists for 128 <= M <= 1024
+    expected = {0, 1} if variant == 1 else ({2} if 128 <= M <= 1024 else {0})
+    assert plan.get_config()["fft_variant"] in expected
     ti = _cuda(idx, torch.int32)
     _check(plan.forward(_cuda(X), ti).cpu().numpy(), oracle.mdc_forward(D, X, idx, 0.5), f"U {shape}")
     _check(plan.adjoint(_cuda(R), ti).cpu().numpy(), oracle.mdc_adjoint(D, R, idx, 0.5), f"G {shape}")
-    # the fused step (model transform kept for the next step) with the reversed order, twice
+    # the fused step (model transform kept for the next step) with this variant, twice
     U_obs = _f32(synth.random_traces((ns, nv, nt), seed + 4))
     alpha = 0.3 / oracle.sigma2_max(D, scale=0.5)
     Xg, Ug = _cuda(X), _cuda(U_obs)
@@ -136,7 +143,7 @@ def test_config_errors():
         plan.set_config(gemm_fwd=binding.MDC_GEMM_TC)
     assert e.value.status == binding.MDC_ERR_UNSUPPORTED
     with pytest.raises(binding.MDCError) as e:
-        plan.set_config(fft_variant=2)
+        plan.set_config(fft_variant=3)
     assert e.value.status == binding.MDC_ERR_INVALID_ARG
     with pytest.raises(binding.MDCError) as e:
         plan.set_config(gemm_adj=7)
