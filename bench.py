@@ -847,8 +847,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
-    ap.add_argument("--autotune", action="store_true",
-                    help="let the plan autotuner choose the FFT radix order and the product kernels")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=True,
+                    help="let the plan autotuner choose the FFT variant and the product kernels (default)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the plans' default kernel configuration")
     ap.add_argument("--batch-n", type=int, default=48, help=f"{BATCH_WORKLOAD}: number of members")
     ap.add_argument("--batch-largest", type=int, default=1,
                     help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")

@@ -38,6 +38,21 @@ struct Fft2 {
     static constexpr size_t SMEM = (size_t)TR * STRIDE * sizeof(float2);
 };
 
+// w_64^m = exp(-2 pi i m / 64) for a compile-time m: the root that steps bin k = t + T m of a team
+// (T / 2M = 1/64), so w_N^k = w_N^t w_64^m with one table load per thread
+__host__ __device__ constexpr float2 root64(int m) {
+    constexpr float c[17] = {1.0f, 0.99518472667219688624f, 0.98078528040323044913f, 0.95694033573220886494f,
+                             0.92387953251128675613f, 0.88192126434835502971f, 0.83146961230254523708f,
+                             0.77301045336273696081f, 0.70710678118654752440f, 0.63439328416364549822f,
+                             0.55557023301960222474f, 0.47139673682599764856f, 0.38268343236508977173f,
+                             0.29028467725446236764f, 0.19509032201612826785f, 0.09801714032956060199f,
+                             0.0f};   // cos(pi j / 32), j = 0..16
+    m &= 63;
+    const int q = m >> 4, rr = m & 15;
+    const float x = c[rr], y = c[16 - rr];   // cos, sin of the angle inside the quadrant
+    return q == 0 ? make_float2(x, -y) : q == 1 ? make_float2(-y, -x) : q == 2 ? make_float2(-x, y) : make_float2(y, x);
+}
+
 // multiply by w_32^m (forward root exp(-2 pi i m / 32); conjugate for INV), m a compile-time constant
 template <bool INV, int MM>
 __device__ __forceinline__ float2 rot32(float2 a) {
@@ -196,12 +211,21 @@ __device__ __forceinline__ void fft2_core(float2 (&a)[32], float2 *buf, int t, c
         for (int r = 0; r < R2; ++r) a[q + Q * r] = buf[pad2(jp + 32 * r)];
     }
     __syncwarp();   // every lane of the team has read buf: the caller may write it again
+    // twiddles w_M^{r j'}: r = r_lo + 8 r_hi, from the table rows r_lo (< 8) and 8 r_hi (each row r holds
+    // w_M^{r j'} for j' < 32): R2/8 + 6 loads and R2 - 8 products instead of R2 - 1 loads
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int jp = t + T * q;
+        constexpr int RL = R2 < 8 ? R2 : 8, RH = R2 / RL;
+        float2 wl[RL], wh[RH];
+#pragma unroll
+        for (int r = 1; r < RL; ++r) wl[r] = __ldg(tw2 + r * 32 + jp);
+#pragma unroll
+        for (int h = 1; h < RH; ++h) wh[h] = __ldg(tw2 + h * RL * 32 + jp);
 #pragma unroll
         for (int r = 1; r < R2; ++r) {
-            const float2 w = __ldg(tw2 + r * 32 + jp);
+            const int lo = r % RL, hi = r / RL;
+            const float2 w = hi == 0 ? wl[lo] : lo == 0 ? wh[hi] : cmul(wl[lo], wh[hi]);
             a[q + Q * r] = INV ? cmulc(a[q + Q * r], w) : cmul(a[q + Q * r], w);
         }
     }
@@ -232,6 +256,7 @@ __device__ __forceinline__ void rfft2_regs_to_smem(float2 (&a)[32], float2 *buf,
     // (pass 2 left buf free: its last reads precede the sync at the end of fft2_core)
     const unsigned lane = threadIdx.x & 31;
     const int src = (int)(lane & ~(unsigned)(T - 1)) + ((T - t) & (T - 1));
+    const float2 wt = __ldg(twN + t);              // w_N^t; w_N^k = w_N^t w_64^m
 #pragma unroll
     for (int m = 0; m < 32; ++m) {
         const float sx = __shfl_sync(0xffffffffu, a[31 - m].x, src);
@@ -239,7 +264,7 @@ __device__ __forceinline__ void rfft2_regs_to_smem(float2 (&a)[32], float2 *buf,
         const float2 zm = (t == 0) ? a[(32 - m) & 31] : make_float2(sx, sy);
         const float2 z = a[m];
         const int k = t + T * m;
-        const float2 wn = __ldg(twN + k);          // w_N^k, N = 2M
+        const float2 wn = cmul(wt, root64(m));     // w_N^k, N = 2M
         const float2 e = cscale(cadd(z, cconj(zm)), 0.5f);
         const float2 d = cmul(wn, cscale(csub(z, cconj(zm)), 0.5f));
         float2 x = cadd(e, mul_mi<false>(d));
@@ -258,6 +283,7 @@ __device__ __forceinline__ void irfft2_smem_to_regs(float2 (&a)[32], float2 *buf
     using F = Fft2<M>;
     constexpr int T = F::T;
     // pre-processing: Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) w_N^{-k}
+    const float2 wt = __ldg(twN + t);
 #pragma unroll
     for (int m = 0; m < 32; ++m) {
         const int k = t + T * m;
@@ -268,7 +294,7 @@ __device__ __forceinline__ void irfft2_smem_to_regs(float2 (&a)[32], float2 *buf
             xk = make_float2(s0.x, 0.f);
             xm = make_float2(s0.y, 0.f);
         }
-        const float2 wn = __ldg(twN + k);
+        const float2 wn = cmul(wt, root64(m));
         const float2 e = cadd(xk, cconj(xm));
         const float2 o = cmulc(csub(xk, cconj(xm)), wn);
         a[m] = cadd(e, mul_mi<true>(o));
