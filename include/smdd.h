@@ -206,11 +206,14 @@ typedef struct {
                           N-SGD or the causality mute run variant 0 whatever is set. */
     int gemm_fwd;      /* MDC_GEMM_SIMT or MDC_GEMM_TC */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
-    int reserved[5];   /* zero */
+    int fft_prefetch;  /* 1: the update runs as persistent CTAs that prefetch the next tile's gradient
+                          spectra while transforming the current one (variants 0 and 1, nfft <= 2048;
+                          elsewhere 0) */
+    int reserved[4];   /* zero */
 } mdc_config;
 
-/* The plan's current configuration (host pointer).  New plans start with fft_variant 0 and the
- * kernels of their precision (SIMT for FP32, TC for BF16X3). */
+/* The plan's current configuration (host pointer).  New plans start with fft_variant 2 for nfft 2048
+ * and 0 otherwise, fft_prefetch 0, and the kernels of their precision (SIMT for FP32, TC for BF16X3). */
 int mdc_plan_get_config(mdc_plan_t plan, mdc_config *cfg);
 /* Set the configuration.  MDC_ERR_INVALID_ARG for an unknown value, MDC_ERR_UNSUPPORTED for
  * MDC_GEMM_TC on an FP32 plan.  Must not be called while work of the plan may still run on the GPU

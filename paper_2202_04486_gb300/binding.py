@@ -67,10 +67,11 @@ class smdd_step_ex_params(ctypes.Structure):
 
 class mdc_config(ctypes.Structure):
     _fields_ = [("fft_variant", ctypes.c_int), ("gemm_fwd", ctypes.c_int), ("gemm_adj", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("fft_prefetch", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
     def as_dict(self) -> dict:
-        return {"fft_variant": self.fft_variant, "gemm_fwd": self.gemm_fwd, "gemm_adj": self.gemm_adj}
+        return {"fft_variant": self.fft_variant, "gemm_fwd": self.gemm_fwd, "gemm_adj": self.gemm_adj,
+                "fft_prefetch": self.fft_prefetch}
 
 
 class smdd_member(ctypes.Structure):
@@ -278,8 +279,8 @@ def mdc_plan_get_config(plan: int) -> dict:
 
 
 def mdc_plan_set_config(plan: int, fft_variant: int = 0, gemm_fwd: int = MDC_GEMM_SIMT,
-                        gemm_adj: int = MDC_GEMM_SIMT) -> None:
-    c = mdc_config(int(fft_variant), int(gemm_fwd), int(gemm_adj))
+                        gemm_adj: int = MDC_GEMM_SIMT, fft_prefetch: int = 0) -> None:
+    c = mdc_config(int(fft_variant), int(gemm_fwd), int(gemm_adj), int(fft_prefetch))
     _check(load_library().mdc_plan_set_config(ctypes.c_void_p(plan), ctypes.byref(c)), "mdc_plan_set_config")
 
 

@@ -61,6 +61,7 @@ struct mdc_plan_s {
     long long launches = 0;
     // kernel configuration (see mdc_config)
     int fft_variant = 0;
+    int fft_prefetch = 0;        // update: persistent CTAs prefetching the next tile (variants 0/1, M <= 1024)
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
     int nf_active = 0;           // band limit of the products (0: every bin)
@@ -108,6 +109,7 @@ FftArgs base_fft(const mdc_plan_s *p) {
     a.nt = p->nt;
     a.tw = p->tw + (p->fft_variant == 2 ? p->tw2_off : p->fft_variant == 1 ? p->tw1_off : 0);
     a.variant = p->fft_variant;
+    a.prefetch = p->fft_prefetch;
     a.twN = p->twN;
     a.s = p->scale / (float)p->nfft;
     a.status = p->status;
@@ -321,6 +323,8 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     p->scale = scale;
     p->prec = precision;
     p->gemm_fwd = p->gemm_adj = (precision == MDC_PREC_BF16X3) ? MDC_GEMM_TC : MDC_GEMM_SIMT;
+    // default FFT: the two-pass form where it measured faster (nfft 2048: update 750 vs 886 us at 301^2)
+    p->fft_variant = (nfft == 2048) ? 2 : 0;
     p->tw1_off = ((fft_tw_size(nfft / 2, 0) > 1 ? fft_tw_size(nfft / 2, 0) : 1) + 1) & ~1;
     p->tw2_off = p->tw1_off + (((fft_tw_size(nfft / 2, 1) > 1 ? fft_tw_size(nfft / 2, 1) : 1) + 1) & ~1);
 
@@ -329,14 +333,15 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     const size_t szX = (size_t)nf * nv * p->ldr * sizeof(float2);
     const size_t szU = (size_t)nf * nv * p->ldb * sizeof(float2);
     {
-        TraceGrid g = batch_grid(p, nb_max);
-        p->resid_blocks_max = fft_blocks(M, g);
-        if (fft2_supported(M)) {   // the residual kernel of every FFT variant fits the partials buffer
+        // the residual kernel of every FFT variant must fit the partials buffer
+        const int v_default = p->fft_variant;
+        p->fft_variant = 0;
+        p->resid_blocks_max = fft_blocks(M, batch_grid(p, nb_max));
+        if (fft2_supported(M)) {
             p->fft_variant = 2;
-            TraceGrid g2 = batch_grid(p, nb_max);
-            p->resid_blocks_max = std::max(p->resid_blocks_max, fft2_blocks(M, g2));
-            p->fft_variant = 0;
+            p->resid_blocks_max = std::max(p->resid_blocks_max, fft2_blocks(M, batch_grid(p, nb_max)));
         }
+        p->fft_variant = v_default;
     }
     bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
               cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw2_off + M + 2) * sizeof(float2)) == cudaSuccess &&
@@ -612,6 +617,7 @@ int mdc_plan_get_config(mdc_plan_t p, mdc_config *cfg) {
     if (!p || !cfg) return MDC_ERR_INVALID_ARG;
     memset(cfg, 0, sizeof(*cfg));
     cfg->fft_variant = p->fft_variant;
+    cfg->fft_prefetch = p->fft_prefetch;
     cfg->gemm_fwd = p->gemm_fwd;
     cfg->gemm_adj = p->gemm_adj;
     return MDC_OK;
@@ -619,15 +625,17 @@ int mdc_plan_get_config(mdc_plan_t p, mdc_config *cfg) {
 
 int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
     if (!p || !cfg) return MDC_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (cfg->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
     if (cfg->fft_variant < 0 || cfg->fft_variant > 2) return MDC_ERR_INVALID_ARG;
+    if (cfg->fft_prefetch != 0 && cfg->fft_prefetch != 1) return MDC_ERR_INVALID_ARG;
     if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
     if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
     if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_adj == MDC_GEMM_TC) && p->prec != MDC_PREC_BF16X3)
         return MDC_ERR_UNSUPPORTED;
     // the spectra a plan holds are the same for both radix orders: switching keeps them valid
     p->fft_variant = fft_has_variant(p->M, cfg->fft_variant) ? cfg->fft_variant : 0;
+    p->fft_prefetch = (p->M <= 1024 && p->fft_variant != 2) ? cfg->fft_prefetch : 0;
     p->gemm_fwd = cfg->gemm_fwd;
     p->gemm_adj = cfg->gemm_adj;
     return MDC_OK;
@@ -679,14 +687,17 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     };
     const bool profiling = p->profiling;
     p->profiling = false;
-    const int old_v = p->fft_variant, old_f = p->gemm_fwd, old_a = p->gemm_adj;
+    const int old_v = p->fft_variant, old_f = p->gemm_fwd, old_a = p->gemm_adj, old_pf = p->fft_prefetch;
     int best_v = old_v, best_f = old_f, best_a = old_a;
     if (rc == MDC_OK) {
         // FFT radix order, on the fused update (inverse + forward transform of every trace)
         double tbest = 1e300;
-        for (int v = 0; v < 3 && rc == MDC_OK; ++v) {
-            if (!fft_has_variant(p->M, v)) continue;
+        int best_pf = 0;
+        for (int cand = 0; cand < 5 && rc == MDC_OK; ++cand) {
+            const int v = cand < 2 ? cand : cand < 4 ? cand - 2 : 2, pf = (cand >= 2 && cand < 4) ? 1 : 0;
+            if (!fft_has_variant(p->M, v) || (pf && p->M > 1024)) continue;
             p->fft_variant = v;
+            p->fft_prefetch = pf;
             const double t = time_it([&] {
                 FftArgs a = base_fft(p);
                 a.g = model_grid(p, nv_sub);
@@ -697,9 +708,10 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
                 return launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, true, a, st); });
             });
             if (t < 0) rc = MDC_ERR_CUDA;
-            else if (t < tbest) { tbest = t; best_v = v; }
+            else if (t < tbest) { tbest = t; best_v = v; best_pf = pf; }
         }
         p->fft_variant = best_v;
+        p->fft_prefetch = best_pf;
     }
     if (rc == MDC_OK) {
         double tbest = 1e300;
@@ -731,6 +743,7 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
         p->gemm_adj = best_a;
     } else {
         p->fft_variant = old_v;
+        p->fft_prefetch = old_pf;
         p->gemm_fwd = old_f;
         p->gemm_adj = old_a;
     }

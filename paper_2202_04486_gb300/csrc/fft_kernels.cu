@@ -12,6 +12,7 @@
 // loader is bound to one trace and issues all of its P global loads before any shared-memory store;
 // time-domain inputs needed after an inverse FFT (the model for the update, the observed data for the
 // residual) are loaded into registers before that FFT starts, so their latency overlaps the passes.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -377,6 +378,120 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
 }
 
 // ------------------------------------------------------------------------------------------------
+// persistent update with a prefetched next tile (M <= 1024): each CTA walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while it transforms one tile, cp.async copies the next tile's gradient
+// spectra into its second buffer, so the CTA keeps HBM reads in flight through its compute phase.
+// ------------------------------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ TileCoord coord_at(const TraceGrid &g, int tile, int tr) {
+    constexpr int TR = Team<M>::TR;
+    const int ti = 1 << g.ti_log2;
+    const int tj = TR >> g.ti_log2;
+    const int ntile_i = (g.ni + ti - 1) / ti;
+    const int bi = tile % ntile_i, bj = tile / ntile_i;
+    TileCoord c;
+    c.i = bi * ti + (tr & (ti - 1));
+    c.j = bj * tj + (tr >> g.ti_log2);
+    c.valid = c.i < g.ni && c.j < g.nj;
+    return c;
+}
+
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+
+// the spectra of `tile` -> buf by cp.async (bin M into the spare slot padi(M); invalid traces
+// zero-filled); one commit group
+template <int M>
+__device__ __forceinline__ void tile_prefetch_spec(float2 *buf, const float2 *__restrict__ spec, const TraceGrid &g, int tile) {
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord c = coord_at<M>(g, tile, tr);
+    const float2 *s = spec + (c.valid ? (long long)c.i * g.ssi + (long long)c.j * g.ssj : 0);
+    const int nbytes = c.valid ? 8 : 0;
+    float2 *b = buf + tr * STR;
+#pragma unroll
+    for (int it = 0; it < P; ++it) {
+        const int f = f0 + it * T;
+        cp_async8(b + padi(f), c.valid ? s + (long long)f * g.ssf : spec, nbytes);
+    }
+    if (f0 == 0) cp_async8(b + padi(M), c.valid ? s + (long long)M * g.ssf : spec, nbytes);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int M>
+__device__ __forceinline__ void tile_store_spec_at(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g, int tile) {
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
+    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
+    const TileCoord c = coord_at<M>(g, tile, tr);
+    if (!c.valid) return;
+    const float2 *b = sm + tr * STR;
+    float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
+#pragma unroll
+    for (int it = 0; it < P; ++it) {
+        const int f = f0 + it * T;
+        const float2 v = (f == 0) ? make_float2(b[0].x, 0.f) : b[padi(f)];
+        s[(long long)f * g.ssf] = v;
+    }
+    if (f0 == 0) s[(long long)M * g.ssf] = make_float2(b[0].y, 0.f);
+}
+
+template <int M, int V, bool KEEP>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(FftArgs a, int ntiles) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int T = Team<M>::T, TR = Team<M>::TR, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
+    constexpr int BUF = TR * Team<M>::STRIDE;
+    const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;   // CTA-uniform
+    tile_prefetch_spec<M>(sm, a.spec, a.g, tile);
+    const float nas = -a.alpha * a.s;
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        float2 *cur = sm + (it & 1) * BUF;
+        const TileCoord c = coord_at<M>(a.g, tile, tr);
+        float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
+        float4 xo[NPAIR];
+        load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();   // this tile's spectra have landed; every thread is done with the previous tile
+        if (threadIdx.x < TR) {   // slot 0 packs (Re X[0], Re X[M])
+            float2 *b = cur + threadIdx.x * Team<M>::STRIDE;
+            b[0] = make_float2(b[0].x, b[padi(M)].x);
+        }
+        __syncthreads();
+        const int nxt = tile + gridDim.x;
+        if (nxt < ntiles) tile_prefetch_spec<M>(sm + ((it + 1) & 1) * BUF, a.spec, a.g, nxt);
+        float2 *buf = cur + tr * Team<M>::STRIDE;
+        float2 v[FFT_P];
+        irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
+#pragma unroll
+        for (int qq = 0; qq < QQ; ++qq)
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) {
+                const int hs = qq * (R / 2) + r;
+                const int i0 = 2 * (2 * t + 2 * T * qq + r * S);
+                const float2 g0 = v[(2 * qq) * R + r], g1 = v[(2 * qq + 1) * R + r];
+                const float4 xv = xo[hs];
+                float4 z;
+                z.x = (i0 < a.nt) ? fmaf(nas, g0.x, xv.x) : 0.f;
+                z.y = (i0 + 1 < a.nt) ? fmaf(nas, g0.y, xv.y) : 0.f;
+                z.z = (i0 + 2 < a.nt) ? fmaf(nas, g1.x, xv.z) : 0.f;
+                z.w = (i0 + 3 < a.nt) ? fmaf(nas, g1.y, xv.w) : 0.f;
+                if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
+                xo[hs] = z;
+            }
+        if constexpr (KEEP) {
+            pairs_to_regs<M, V>(xo, v);
+            team_sync<T>();
+            rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
+            __syncthreads();
+            tile_store_spec_at<M>(cur, a.spec, a.g, tile);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
 #define SMDD_SWITCH_M(M_, ...)                                    \
@@ -484,6 +599,14 @@ static cudaError_t prepare_m() {
         });
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if constexpr (M <= 1024) {
+        for (int v = 0; v < 2; ++v)
+            with_variant<M>(v, [&](auto vc) {
+                constexpr int V = decltype(vc)::value;
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_pf<M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sm);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_pf<M, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sm);
+            });
+    }
     return e;
 }
 
@@ -532,12 +655,35 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
     return cudaGetLastError();
 }
 
+// the persistent prefetching update (M <= 1024): as many CTAs as fit on the GPU at once, each walking
+// the tiles; returns false (nothing launched) for larger M
+template <int M>
+static bool launch_update_pf(bool keep, const FftArgs &a, int ntiles, cudaStream_t st) {
+    if constexpr (M <= 1024) {
+        with_variant<M>(a.variant, [&](auto vc) {
+            constexpr int V = decltype(vc)::value;
+            auto kern = keep ? k_update_pf<M, V, true> : k_update_pf<M, V, false>;
+            int per_sm = 0, dev = 0, nsm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Team<M>::THREADS, 2 * Team<M>::SMEM);
+            const int grid = std::max(1, std::min(ntiles, std::max(1, per_sm) * std::max(1, nsm)));
+            kern<<<grid, Team<M>::THREADS, 2 * Team<M>::SMEM, st>>>(a, ntiles);
+        });
+        return true;
+    } else {
+        return false;
+    }
+}
+
 cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     if (a.variant == 2 && !a.vel && !a.mute) return launch2_update(M, keep, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb == 0) return cudaSuccess;
-        if (a.vel || a.mute) {
+        if (a.prefetch && !a.vel && !a.mute && launch_update_pf<MM>(keep, a, nb, st)) {
+            // persistent, prefetching form launched
+        } else if (a.vel || a.mute) {
             // momentum / causality mute: radix order 0 only (the caller passes its twiddle table)
             if (a.variant != 0) return cudaErrorInvalidValue;
             if (keep) k_update<MM, 0, true, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);

@@ -49,6 +49,7 @@ struct FftArgs {
     float *vel;
     float mu;
     const int32_t *mute;
+    int prefetch;            // update: persistent CTAs prefetching the next tile's spectra (M <= 1024)
 };
 
 struct GemmArgs {

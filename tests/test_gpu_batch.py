@@ -59,7 +59,7 @@ VARIANT_SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, "prefetch0", "prefetch1"])
 @pytest.mark.parametrize("shape", VARIANT_SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_fft_variants_match_oracle(shape, variant):
     nt, nr, nv, ns, nb = shape
@@ -69,11 +69,16 @@ def test_fft_variants_match_oracle(shape, variant):
     R = _f32(synth.random_traces((nb, nv, nt), seed + 2))
     idx = synth.random_indices(ns, nb, seed + 3)
     plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, scale=0.5)
-    plan.set_config(fft_variant=variant)
     M = plan.nfft // 2
-    # variant 1 falls back to 0 where both radix orders coincide; variant 2 exists for 128 <= M <= 1024
-    expected = {0, 1} if variant == 1 else ({2} if 128 <= M <= 1024 else {0})
-    assert plan.get_config()["fft_variant"] in expected
+    if isinstance(variant, str):   # the persistent prefetching update with radix order 0 or 1
+        order = int(variant[-1])
+        plan.set_config(fft_variant=order, fft_prefetch=1)
+        assert plan.get_config()["fft_prefetch"] == (1 if M <= 1024 else 0)
+    else:
+        plan.set_config(fft_variant=variant)
+        # variant 1 falls back to 0 where both radix orders coincide; variant 2 exists for 128 <= M <= 1024
+        expected = {0, 1} if variant == 1 else ({2} if 128 <= M <= 1024 else {0})
+        assert plan.get_config()["fft_variant"] in expected
     ti = _cuda(idx, torch.int32)
     _check(plan.forward(_cuda(X), ti).cpu().numpy(), oracle.mdc_forward(D, X, idx, 0.5), f"U {shape}")
     _check(plan.adjoint(_cuda(R), ti).cpu().numpy(), oracle.mdc_adjoint(D, R, idx, 0.5), f"G {shape}")
@@ -138,7 +143,8 @@ def test_config_errors():
     D = _cuda(synth.random_traces((4, 3, 16), 1))
     plan = binding.MDCPlan(D, 3, nb_max=2)
     cfg = plan.get_config()
-    assert cfg == {"fft_variant": 0, "gemm_fwd": binding.MDC_GEMM_SIMT, "gemm_adj": binding.MDC_GEMM_SIMT}
+    assert cfg == {"fft_variant": 0, "gemm_fwd": binding.MDC_GEMM_SIMT, "gemm_adj": binding.MDC_GEMM_SIMT,
+                   "fft_prefetch": 0}
     with pytest.raises(binding.MDCError) as e:
         plan.set_config(gemm_fwd=binding.MDC_GEMM_TC)
     assert e.value.status == binding.MDC_ERR_UNSUPPORTED
@@ -153,7 +159,8 @@ def test_config_errors():
     assert e.value.status == binding.MDC_ERR_SHAPE
     assert plan.get_config() == cfg
     b16 = binding.MDCPlan(D, 3, nb_max=2, precision=binding.MDC_PREC_BF16X3)
-    assert b16.get_config() == {"fft_variant": 0, "gemm_fwd": binding.MDC_GEMM_TC, "gemm_adj": binding.MDC_GEMM_TC}
+    assert b16.get_config() == {"fft_variant": 0, "gemm_fwd": binding.MDC_GEMM_TC, "gemm_adj": binding.MDC_GEMM_TC,
+                                "fft_prefetch": 0}
 
 
 @pytest.mark.parametrize("precision", [binding.MDC_PREC_FP32, binding.MDC_PREC_BF16X3])
