@@ -605,11 +605,34 @@ def solver_comparison(args, dev, D, U_obs, X_true, w, rank):
             raise RuntimeError(f"device status after {solver}")
         res[solver] = {"model_error_at_epoch": {k: round(e, 5) for k, e in errs}, "device_s": round(t, 4)}
         plan.close()
+    # batch-size sweep of SGD (same epochs, alpha = 0.5 * 2/sigma^2 for every batch size)
+    sweep = {}
+    for nbs in sorted({4, 8, nb, 2 * nb, 4 * nb} & set(range(1, ns + 1))):
+        plan = binding.MDCPlan(D, nv, nb_max=nbs)
+        alpha = 0.5 * 2.0 / plan.sigma2_max(60)
+        X = torch.zeros((nv, nr, nt), device=dev)
+        bl = synth.epoch_batches(ns, nbs, n_ep, seed=300 + rank)
+        k, t = 0, 0.0
+        e0.record()
+        for ep in bl:
+            for b in ep:
+                fl = rflag | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+                binding.smdd_step(plan.handle, X, U_obs, torch.from_numpy(b).to(dev), alpha, fl)
+                k += 1
+        e1.record()
+        torch.cuda.synchronize()
+        if plan.sync_status() != binding.MDC_OK:
+            raise RuntimeError("device status after the batch-size sweep")
+        sweep[str(nbs)] = {"model_error": round((X.double() - xt).norm().item() / xt_norm, 5),
+                           "steps": k, "device_s": round(e0.elapsed_time(e1) / 1e3, 4)}
+        plan.close()
+    res["sgd_batch_size_sweep"] = sweep
     target = res["sgd"]["model_error_at_epoch"][n_ep]
     for solver in ("sgd", "nsgd", "lsqr"):
         errs = res[solver]["model_error_at_epoch"]
         res[solver]["epochs_to_sgd_final_error"] = next((k for k in sorted(errs) if errs[k] <= target), None)
-    res["definition"] = ("model error = ||X - X_true|| / ||X_true|| after each epoch; an epoch is ceil(ns/nb) "
+    res["definition"] = ("model error = ||X - X_true|| / ||X_true|| after each epoch (the batch-size sweep: after "
+                         f"all {n_ep} epochs); an epoch is ceil(ns/nb) "
                          "stochastic steps or one LSQR iteration (every source once); LSQR is evaluated at "
                          f"checkpoint iteration counts, each run from zero; LSQR device_s is for {n_ep} iterations")
     return res
