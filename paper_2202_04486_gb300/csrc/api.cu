@@ -546,8 +546,13 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
     // a7 + a8: inverse FFT, window, update, and optionally the spectra of the new model
     {
         const bool keep = flags & SMDD_KEEP_XHAT;
+        // the momentum / mute update exists for the default radix order only: lay its grid out (and take
+        // its twiddle table) for FFT variant 0, whatever the plan's variant
+        const int v_plan = p->fft_variant;
+        if (vel || mute) p->fft_variant = 0;
         FftArgs a = base_fft(p);
         a.g = model_grid(p, p->nv);
+        p->fft_variant = v_plan;
         a.tout = X;
         a.vec = vec4_ok(p->nt, X) && (vel == nullptr || vec4_ok(p->nt, vel));
         a.spec = p->Xh;
@@ -555,10 +560,6 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         a.vel = vel;
         a.mu = mu;
         a.mute = mute;
-        if (vel || mute) {   // the momentum / mute update is built for the default radix order only
-            a.variant = 0;
-            a.tw = p->tw;
-        }
         if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;
         if (keep) p->xhat_for = X;
     }

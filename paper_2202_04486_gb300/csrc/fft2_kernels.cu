@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_update(FftArgs a) {
 
 template <int M>
 int blocks2_for(const TraceGrid &g) {
+    // -1: the grid was laid out for CTAs of another trace count (more traces along i than a CTA holds)
     const int ti = 1 << g.ti_log2, tj = Fft2<M>::TR >> g.ti_log2;
+    if (tj < 1) return -1;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
 }
 
@@ -325,6 +327,7 @@ cudaError_t fft2_prepare(int M) {
 cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M2(M, {
         const int nb = blocks2_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         k2_rfft<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
     });
@@ -334,6 +337,7 @@ cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st) {
 cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M2(M, {
         const int nb = blocks2_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         k2_irfft_out<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
     });
@@ -343,7 +347,7 @@ cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
 cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st) {
     SMDD_SWITCH_M2(M, {
         const int nb = blocks2_for<MM>(a.g);
-        if (nb == 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
+        if (nb <= 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
         k2_residual<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
@@ -352,6 +356,7 @@ cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cuda
 cudaError_t launch2_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     SMDD_SWITCH_M2(M, {
         const int nb = blocks2_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         if (keep) k2_update<MM, true><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
         else k2_update<MM, false><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);

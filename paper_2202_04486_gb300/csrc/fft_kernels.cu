@@ -509,7 +509,9 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
 
 template <int M>
 static int blocks_for(const TraceGrid &g) {
+    // -1: the grid was laid out for CTAs of another trace count (more traces along i than a CTA holds)
     const int ti = 1 << g.ti_log2, tj = Team<M>::TR >> g.ti_log2;
+    if (tj < 1) return -1;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
 }
 
@@ -623,6 +625,7 @@ cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st) {
     if (a.variant == 2) return launch2_rfft(M, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         with_variant<MM>(a.variant, [&](auto vc) {
             k_rfft<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
@@ -635,6 +638,7 @@ cudaError_t launch_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
     if (a.variant == 2) return launch2_irfft_out(M, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         with_variant<MM>(a.variant, [&](auto vc) {
             k_irfft_out<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
@@ -647,7 +651,7 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
     if (a.variant == 2) return launch2_residual(M, a, nblocks_expected, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
-        if (nb == 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
+        if (nb <= 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
         with_variant<MM>(a.variant, [&](auto vc) {
             k_residual<MM, decltype(vc)::value><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
         });
@@ -680,6 +684,7 @@ cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     if (a.variant == 2 && !a.vel && !a.mute) return launch2_update(M, keep, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
+        if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
         if (a.prefetch && !a.vel && !a.mute && launch_update_pf<MM>(keep, a, nb, st)) {
             // persistent, prefetching form launched

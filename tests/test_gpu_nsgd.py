@@ -162,3 +162,28 @@ def test_step_ex_host_errors():
         binding.smdd_step_ex(p2.handle, torch.zeros((3, 4, 16), device="cuda"), torch.zeros((5, 3, 16), device="cuda"),
                              idx, 0.1, binding.SMDD_RECIPROCITY)
     assert e.value.status == binding.MDC_ERR_SHAPE
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_nsgd_and_mute_under_every_fft_variant(variant):
+    """The momentum / mute update runs the default radix order whatever FFT variant the plan holds; the
+    other kernels of the step run the plan's variant.  Both must agree on the trace tiling."""
+    nt, n, ns, nb = 257, 12, 15, 5        # nfft 1024: all three variants exist
+    p = synth.make_problem(nt, n, n, ns, dx=60.0, n_reflectors=3, n_multiples=2, seed=77)
+    D = _f32(p.D)
+    U_obs = _f32(oracle.mdc_forward(D, _f32(p.X_true), np.arange(ns)))
+    mute = synth.direct_arrival_mute(n, n, nt, dx=60.0)
+    alpha, mu = 0.4 / oracle.sigma2_max(D), 0.9
+    plan = binding.MDCPlan(_cuda(D), n, nb_max=nb)
+    plan.set_config(fft_variant=variant)
+    X, V = np.zeros((n, n, nt)), np.zeros((n, n, nt))
+    Xg, Vg = _cuda(X), _cuda(V)
+    for k in range(2):
+        idx = synth.random_indices(ns, nb, 80 + k)
+        fl = binding.SMDD_RECIPROCITY | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+        binding.smdd_step_ex(plan.handle, Xg, _cuda(U_obs), _cuda(idx, torch.int32), alpha, fl | binding.SMDD_NESTEROV,
+                             V=Vg, mu=mu, mute=_cuda(mute, torch.int32))
+        X, V, _ = oracle.nsgd_step(D, X, V, U_obs, idx, alpha, mu, recip=True, mute=mute)
+    assert plan.sync_status() == binding.MDC_OK
+    _check(Xg.cpu().numpy(), X, f"X (variant {variant})")
+    _check(Vg.cpu().numpy(), V, f"V (variant {variant})")
