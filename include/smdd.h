@@ -197,6 +197,10 @@ int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float 
 #define MDC_GEMM_SIMT32  1   /* adjoint only: FP32 FMA, 32 x 32 output tiles */
 #define MDC_GEMM_SIMT64  2   /* adjoint only: FP32 FMA, 64 x 64 output tiles */
 #define MDC_GEMM_TC      3   /* split-BF16 tcgen05 kernels (MDC_PREC_BF16X3 plans only) */
+#define MDC_GEMM_GEMV    4   /* FP32 matrix-vector kernels for few virtual sources (nv <= 8): a warp or a
+                                thread streams each gathered kernel row once.  Used where allowed: with
+                                a band limit, and for the adjoint with reciprocity, the call runs
+                                MDC_GEMM_SIMT instead. */
 
 typedef struct {
     int fft_variant;   /* 0: default radix order of the FFT plan; 1: the reversed order (accepted for
@@ -222,8 +226,8 @@ int mdc_plan_get_config(mdc_plan_t plan, mdc_config *cfg);
 int mdc_plan_set_config(mdc_plan_t plan, const mdc_config *cfg);
 /* Autotune: time every candidate of each choice on this plan's sizes, with batch size nb and the
  * step flags (SMDD_RECIPROCITY changes the adjoint), reps timed launches each after one warm-up, and
- * keep the fastest.  The FFT candidates are timed on the fused update kernel over a subset of at most
- * 64 MiB of model traces.  best (host, may be NULL) receives the chosen configuration.
+ * keep the fastest.  The FFT candidates are timed on a step's two trace kernels: the fused update over a
+ * subset of at most 64 MiB of model traces (scaled to all of them) plus the residual step of one batch.  best (host, may be NULL) receives the chosen configuration.
  * Uses temporary device memory (cudaMalloc), overwrites the plan's spectral workspaces, synchronises
  * the stream, and must not be called during a stream capture. */
 int mdc_plan_autotune(mdc_plan_t plan, int nb, int flags, int reps, mdc_config *best, void *stream);

@@ -184,6 +184,8 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.nf_active = p->nf_active;
     if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
+    if (p->gemm_fwd == MDC_GEMM_GEMV && gemv_supported(p->nv) && p->nf_active == 0)
+        return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_gemv_fwd(g, p->nf, st); });
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
 }
 
@@ -203,6 +205,8 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.nf_active = p->nf_active;
     if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
+    if (p->gemm_adj == MDC_GEMM_GEMV && gemv_supported(p->nv) && !recip && p->nf_active == 0 && nb <= 1024)
+        return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_gemv_adj(g, p->nf, st); });
     const int tile = p->gemm_adj == MDC_GEMM_SIMT32 ? 32 : p->gemm_adj == MDC_GEMM_SIMT64 ? 64 : 0;
     return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_cgemm_adj(g, recip, p->nf, st, tile); });
 }
@@ -630,8 +634,11 @@ int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
         if (cfg->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
     if (cfg->fft_variant < 0 || cfg->fft_variant > 2) return MDC_ERR_INVALID_ARG;
     if (cfg->fft_prefetch != 0 && cfg->fft_prefetch != 1) return MDC_ERR_INVALID_ARG;
-    if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
-    if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_TC) return MDC_ERR_INVALID_ARG;
+    if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC && cfg->gemm_fwd != MDC_GEMM_GEMV)
+        return MDC_ERR_INVALID_ARG;
+    if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_GEMV) return MDC_ERR_INVALID_ARG;
+    if ((cfg->gemm_fwd == MDC_GEMM_GEMV || cfg->gemm_adj == MDC_GEMM_GEMV) && !gemv_supported(p->nv))
+        return MDC_ERR_UNSUPPORTED;
     if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_adj == MDC_GEMM_TC) && p->prec != MDC_PREC_BF16X3)
         return MDC_ERR_UNSUPPORTED;
     // the spectra a plan holds are the same for both radix orders: switching keeps them valid
@@ -658,20 +665,23 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     const long long trace_bytes = (long long)p->nr * p->nt * (long long)sizeof(float);
     const int nv_sub = (int)std::max(1LL, std::min((long long)p->nv, (64LL << 20) / std::max(1LL, trace_bytes)));
     int32_t *didx = nullptr;
-    float *xs = nullptr;
+    float *xs = nullptr, *us = nullptr;   // model-trace subset; gathered observed rows of one batch
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = MDC_OK;
     std::vector<int32_t> hidx(nb);
     for (int i = 0; i < nb; ++i) hidx[i] = i % p->ns;
+    const size_t u_bytes = (size_t)nb * p->nv * p->nt * sizeof(float);
     if (cudaMalloc(&didx, nb * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&xs, (size_t)nv_sub * trace_bytes) != cudaSuccess) {
+        cudaMalloc(&xs, (size_t)nv_sub * trace_bytes) != cudaSuccess || cudaMalloc(&us, u_bytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(didx);
         cudaFree(xs);
+        cudaFree(us);
         return MDC_ERR_OOM;
     }
     if (cudaMemcpyAsync(didx, hidx.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(xs, 0, (size_t)nv_sub * trace_bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaMemsetAsync(xs, 0, (size_t)nv_sub * trace_bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(us, 0, u_bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess)
         rc = MDC_ERR_CUDA;
 
@@ -699,7 +709,9 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
             if (!fft_has_variant(p->M, v) || (pf && p->M > 1024)) continue;
             p->fft_variant = v;
             p->fft_prefetch = pf;
-            const double t = time_it([&] {
+            // a step's two trace kernels: the fused update (scaled from the model subset to every model
+            // trace) and the residual step of one batch
+            const double tu = time_it([&] {
                 FftArgs a = base_fft(p);
                 a.g = model_grid(p, nv_sub);
                 a.tout = xs;
@@ -708,6 +720,23 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
                 a.alpha = 0.f;
                 return launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, true, a, st); });
             });
+            const double tr = tu < 0 ? -1.0 : time_it([&] {
+                FftArgs a = base_fft(p);
+                a.g = batch_grid(p, nb);
+                a.spec = p->Uh;
+                a.uobs = us;
+                a.idx = didx;
+                a.ns = p->ns;
+                a.gathered = 1;
+                a.uo_si = (long long)p->nv * p->nt;
+                a.uo_sj = p->nt;
+                a.vec = vec4_ok(p->nt, us);
+                a.partials = p->partials;
+                a.counter = p->counter;
+                a.loss = nullptr;
+                return launch_stage(p, ST_RESID, st, [&] { return launch_residual(p->M, a, p->resid_blocks_max, st); });
+            });
+            const double t = (tu < 0 || tr < 0) ? -1.0 : tu * ((double)p->nv / nv_sub) + tr;
             if (t < 0) rc = MDC_ERR_CUDA;
             else if (t < tbest) { tbest = t; best_v = v; best_pf = pf; }
         }
@@ -716,9 +745,10 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     }
     if (rc == MDC_OK) {
         double tbest = 1e300;
-        const int cand[2] = {MDC_GEMM_SIMT, MDC_GEMM_TC};
+        const int cand[3] = {MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_GEMV};
         for (int c : cand) {
             if (c == MDC_GEMM_TC && p->prec != MDC_PREC_BF16X3) continue;
+            if (c == MDC_GEMM_GEMV && !gemv_supported(p->nv)) continue;
             p->gemm_fwd = c;
             const double t = time_it([&] { return gemm_forward(p, didx, nb, st); });
             if (t < 0) { rc = MDC_ERR_CUDA; break; }
@@ -727,9 +757,10 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     }
     if (rc == MDC_OK) {
         double tbest = 1e300;
-        const int cand[3] = {MDC_GEMM_SIMT32, MDC_GEMM_SIMT64, MDC_GEMM_TC};
+        const int cand[4] = {MDC_GEMM_SIMT32, MDC_GEMM_SIMT64, MDC_GEMM_TC, MDC_GEMM_GEMV};
         for (int c : cand) {
             if (c == MDC_GEMM_TC && p->prec != MDC_PREC_BF16X3) continue;
+            if (c == MDC_GEMM_GEMV && (!gemv_supported(p->nv) || recip)) continue;
             p->gemm_adj = c;
             const double t = time_it([&] { return gemm_adjoint(p, didx, nb, recip, st); });
             if (t < 0) { rc = MDC_ERR_CUDA; break; }
@@ -753,6 +784,7 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     if (e1) cudaEventDestroy(e1);
     cudaFree(didx);
     cudaFree(xs);
+    cudaFree(us);
     if (rc == MDC_OK && best) mdc_plan_get_config(p, best);
     return rc;
 }

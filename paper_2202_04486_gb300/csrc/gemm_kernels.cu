@@ -370,6 +370,122 @@ __global__ void __launch_bounds__(AdjGeom<TT>::THREADS, TT == 64 ? 3 : 8) k_cgem
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Few virtual sources (nv <= 8, the matrix-vector regime of a single-virtual-source inversion): the
+// products are bound by reading the batch rows of Dh once, so a warp streams one kernel row against
+// the nv model rows (forward) or a thread owns one receiver and walks the batch (adjoint).
+// ------------------------------------------------------------------------------------------------
+constexpr int GV_THREADS = 256, GV_MAXV = 8;
+
+// forward: C[f][v][b] = sum_r A[f][v][r] Dh[f][idx_b][r]; one warp per batch entry b
+template <int NV>
+__global__ void __launch_bounds__(GV_THREADS) k_gemv_fwd(GemmArgs a) {
+    const int f = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.y * (GV_THREADS / 32) + warp;
+    if (b >= a.nb) return;   // warp-uniform; no barrier in this kernel
+    int s = a.idx[b];
+    if (s < 0 || s >= a.ns) {
+        if (lane == 0) atomicOr(a.status, 1);
+        s = -1;
+    }
+    const float2 *Af = a.A + (long long)f * a.sAf;
+    float2 acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = make_float2(0.f, 0.f);
+    if (s >= 0) {
+        const float2 *d = a.Dh + (long long)f * a.sDf + (long long)s * a.ldr;
+        for (int r = lane; r < a.nr; r += 32) {
+            const float2 dv = __ldg(d + r);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (v < a.nv) {
+                    const float2 x = __ldg(Af + (long long)v * a.ldr + r);
+                    acc[v].x = fmaf(x.x, dv.x, fmaf(-x.y, dv.y, acc[v].x));
+                    acc[v].y = fmaf(x.x, dv.y, fmaf(x.y, dv.x, acc[v].y));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[v].x += __shfl_down_sync(0xffffffffu, acc[v].x, o);
+            acc[v].y += __shfl_down_sync(0xffffffffu, acc[v].y, o);
+        }
+    if (lane == 0) {
+        float2 *Cf = a.C + (long long)f * a.sCf;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if (v < a.nv) Cf[(long long)v * a.ldb + b] = make_float2(acc[v].x * a.outscale, acc[v].y * a.outscale);
+    }
+}
+
+// adjoint (no reciprocity): C[f][v][r] = outscale * sum_b A[f][v][b] conj(Dh[f][idx_b][r]); one thread
+// per receiver r, the batch walked in order (the coefficients are warp-uniform broadcasts)
+template <int NV>
+__global__ void __launch_bounds__(GV_THREADS) k_gemv_adj(GemmArgs a) {
+    __shared__ int sidx[AD_MAXNB];
+    const int f = blockIdx.x, r = blockIdx.y * GV_THREADS + threadIdx.x;
+    for (int b = threadIdx.x; b < a.nb; b += GV_THREADS) {
+        int s = a.idx[b];
+        if (s < 0 || s >= a.ns) {
+            atomicOr(a.status, 1);
+            s = -1;
+        }
+        sidx[b] = s;
+    }
+    __syncthreads();
+    if (r >= a.nr) return;   // after the only barrier
+    const float2 *Af = a.A + (long long)f * a.sAf;
+    const float2 *Df = a.Dh + (long long)f * a.sDf;
+    float2 acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = make_float2(0.f, 0.f);
+    for (int b = 0; b < a.nb; ++b) {
+        const int s = sidx[b];
+        if (s < 0) continue;
+        const float2 d = __ldg(Df + (long long)s * a.ldr + r);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < a.nv) {
+                const float2 c = __ldg(Af + (long long)v * a.ldb + b);
+                // c * conj(d)
+                acc[v].x = fmaf(c.x, d.x, fmaf(c.y, d.y, acc[v].x));
+                acc[v].y = fmaf(c.y, d.x, fmaf(-c.x, d.y, acc[v].y));
+            }
+        }
+    }
+    float2 *Cf = a.C + (long long)f * a.sCf;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        if (v < a.nv) Cf[(long long)v * a.ldr + r] = make_float2(acc[v].x * a.outscale, acc[v].y * a.outscale);
+}
+
+bool gemv_supported(int nv) { return nv >= 1 && nv <= GV_MAXV; }
+
+cudaError_t launch_gemv_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
+    if (!gemv_supported(a.nv) || nf < 1) return cudaErrorInvalidValue;
+    if (a.nf_active > 0 && a.nf_active < nf) return cudaErrorInvalidValue;   // band limits use the tiled kernels
+    const dim3 grid(nf, (a.nb + GV_THREADS / 32 - 1) / (GV_THREADS / 32));
+    if (a.nv == 1) k_gemv_fwd<1><<<grid, GV_THREADS, 0, st>>>(a);
+    else if (a.nv <= 2) k_gemv_fwd<2><<<grid, GV_THREADS, 0, st>>>(a);
+    else if (a.nv <= 4) k_gemv_fwd<4><<<grid, GV_THREADS, 0, st>>>(a);
+    else k_gemv_fwd<8><<<grid, GV_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_adj(const GemmArgs &a, int nf, cudaStream_t st) {
+    if (!gemv_supported(a.nv) || nf < 1 || a.nb > AD_MAXNB) return cudaErrorInvalidValue;
+    if (a.nf_active > 0 && a.nf_active < nf) return cudaErrorInvalidValue;
+    const dim3 grid(nf, (a.nr + GV_THREADS - 1) / GV_THREADS);
+    if (a.nv == 1) k_gemv_adj<1><<<grid, GV_THREADS, 0, st>>>(a);
+    else if (a.nv <= 2) k_gemv_adj<2><<<grid, GV_THREADS, 0, st>>>(a);
+    else if (a.nv <= 4) k_gemv_adj<4><<<grid, GV_THREADS, 0, st>>>(a);
+    else k_gemv_adj<8><<<grid, GV_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_prepare() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_cgemm_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FW_SMEM))) return e;

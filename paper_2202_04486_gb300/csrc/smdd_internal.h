@@ -101,6 +101,10 @@ cudaError_t launch2_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t
 cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, int tile = 0);
 cudaError_t gemm_prepare();
+// few virtual sources (nv <= 8): matrix-vector kernels; no band limit, no reciprocity (adjoint)
+bool gemv_supported(int nv);
+cudaError_t launch_gemv_fwd(const GemmArgs &a, int nf, cudaStream_t st);
+cudaError_t launch_gemv_adj(const GemmArgs &a, int nf, cudaStream_t st);
 
 // split-BF16 tensor-core products (tcgen05)
 cudaError_t tc_prepare();

@@ -64,3 +64,44 @@ def test_single_virtual_source(precision):
     assert plan.sync_status() == binding.MDC_OK and plan2.sync_status() == binding.MDC_OK
     assert oracle.rel_l2(Xs.double().cpu().numpy(), Xr) <= tol
     assert oracle.rel_l2(Xn.double().cpu().numpy(), Xnr) <= tol
+
+
+@pytest.mark.parametrize("shape", [(1024, 180, 1, 110, 16), (257, 37, 3, 41, 7), (130, 8, 8, 12, 5), (64, 70, 5, 80, 70)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_matrix_vector_kernels(shape):
+    """The matrix-vector products for few virtual sources (MDC_GEMM_GEMV) against the oracle; with
+    reciprocity (nr = nv <= 8) and with a band limit the call falls back to the tiled kernels."""
+    nt, nr, nv, ns, nb = shape
+    seed = sum(shape)
+    D = synth.random_traces((ns, nr, nt), seed).astype(np.float32).astype(np.float64)
+    X = synth.random_traces((nv, nr, nt), seed + 1).astype(np.float32).astype(np.float64)
+    R = synth.random_traces((nb, nv, nt), seed + 2).astype(np.float32).astype(np.float64)
+    idx = synth.random_indices(ns, nb, seed + 3, replace=nb > ns)
+    plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb)
+    plan.set_config(gemm_fwd=binding.MDC_GEMM_GEMV, gemm_adj=binding.MDC_GEMM_GEMV)
+    ti = _cuda(idx, torch.int32)
+    U = plan.forward(_cuda(X), ti).double().cpu().numpy()
+    G = plan.adjoint(_cuda(R), ti).double().cpu().numpy()
+    assert plan.sync_status() == binding.MDC_OK
+    U_ref, G_ref = oracle.mdc_forward(D, X, idx), oracle.mdc_adjoint(D, R, idx)
+    assert oracle.rel_l2(U, U_ref) <= 1e-5 and np.max(np.abs(U - U_ref)) <= 2e-5 * np.max(np.abs(U_ref))
+    assert oracle.rel_l2(G, G_ref) <= 1e-5 and np.max(np.abs(G - G_ref)) <= 2e-5 * np.max(np.abs(G_ref))
+    if nr == nv:   # reciprocity step: the adjoint runs the tiled kernel
+        U_obs = synth.random_traces((ns, nv, nt), seed + 4).astype(np.float32).astype(np.float64)
+        alpha = 0.3 / oracle.sigma2_max(D)
+        Xg = _cuda(X)
+        binding.smdd_step(plan.handle, Xg, _cuda(U_obs), ti, alpha, binding.SMDD_RECIPROCITY)
+        Xr, _ = oracle.sgd_step(D, X, U_obs, idx, alpha, recip=True)
+        assert plan.sync_status() == binding.MDC_OK
+        assert oracle.rel_l2(Xg.double().cpu().numpy(), Xr) <= 1e-5
+    plan.set_band(plan.nf // 2)          # band limit: the tiled kernels, with zero bins above the band
+    Ub = plan.forward(_cuda(X), ti).double().cpu().numpy()
+    assert oracle.rel_l2(Ub, oracle.mdc_forward_fft(D, X, idx, band=plan.nf // 2)) <= 1e-5
+
+
+def test_matrix_vector_kernels_need_few_virtual_sources():
+    D = _cuda(synth.random_traces((5, 4, 16), 9))
+    plan = binding.MDCPlan(D, 9, nb_max=2)
+    with pytest.raises(binding.MDCError) as e:
+        plan.set_config(gemm_fwd=binding.MDC_GEMM_GEMV)
+    assert e.value.status == binding.MDC_ERR_UNSUPPORTED
