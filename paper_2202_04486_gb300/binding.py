@@ -400,6 +400,14 @@ class MDCPlan:
     def step(self, X, U_obs, idx, alpha, flags=0, loss=None):
         smdd_step(self.handle, X, U_obs, idx, alpha, flags, loss)
 
+    def step_nsgd(self, X, V, U_obs, idx, alpha, mu=0.9, flags=0, mute=None, loss=None):
+        """N-SGD step (Nesterov momentum, velocity V) with the optional causality mute."""
+        smdd_step_ex(self.handle, X, U_obs, idx, alpha, flags | SMDD_NESTEROV, V=V, mu=mu, mute=mute, loss=loss)
+
+    def lsqr(self, X, U_obs, n_iter, flags=0, mute=None, norms=None):
+        """Full-gradient LSQR over every source (the plan needs nb_max >= ns); X: start in, solution out."""
+        smdd_lsqr(self.handle, X, U_obs, n_iter, flags, mute, norms)
+
     def sync_status(self) -> int:
         return mdc_plan_sync_status(self.handle)
 
