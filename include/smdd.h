@@ -89,7 +89,9 @@ int mdc_plan_info(mdc_plan_t plan, int *nfft, int *nf);
 /* Largest squared singular value of the frequency-domain kernel, max over bins f of
  * lambda_max(Dh_f^H Dh_f) * scale^2, by n_iter power iterations per bin (Appendix B: the singular
  * values of the MDC operator are those of the kernel; alpha_max = 2 / sigma^2 for the Landweber
- * iteration).  The result is a lower bound of the exact value that converges as n_iter grows.
+ * iteration).  The result is a lower bound of the exact value that converges as n_iter grows (the
+ * products run in FP32, the norms in FP64: the rounding moves it by ~1e-6 relative).  Needs
+ * (2*nr + ns) * 8 bytes of shared memory per bin (MDC_ERR_UNSUPPORTED above 227 KiB).
  * Blocks until the value is on the host.  sigma2 is a host pointer. */
 int mdc_plan_sigma2_max(mdc_plan_t plan, int n_iter, double *sigma2, void *stream);
 

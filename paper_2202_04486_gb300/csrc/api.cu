@@ -440,7 +440,7 @@ int mdc_plan_info(mdc_plan_t p, int *nfft, int *nf) {
 
 int mdc_plan_sigma2_max(mdc_plan_t p, int n_iter, double *sigma2, void *stream) {
     if (!p || !sigma2 || n_iter < 1) return MDC_ERR_INVALID_ARG;
-    if ((size_t)(2 * p->nr + p->ns) * 16 > 227 * 1024) return MDC_ERR_UNSUPPORTED;
+    if ((size_t)(2 * p->nr + p->ns) * sizeof(float2) > 227 * 1024) return MDC_ERR_UNSUPPORTED;
     DeviceGuard dg(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     int rc = launch_stage(p, ST_SETUP, st, [&] {
