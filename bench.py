@@ -462,7 +462,10 @@ def run_gpu(args, rank, world, w):
                        "share": round(v[0] / sum(x[0] for x in st.values()), 4)} for k, v in st.items()}
 
     # step-level roofline: max(compulsory bytes / HBM, flops / FP32 ALU peak)
-    fp32_peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    # FP32 peak: measured FMA throughput (probe launched after the timed region), lane count x clock beside it
+    fp32_derived = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = binding.alu_peak_tflops(0)
+    fp64_peak = binding.alu_peak_tflops(1)
     t_roof = max(step_bytes_compulsory(nt, nr, nv, nb, recip) / (peaks["hbm_gbs"] * 1e9),
                  step_flops(nt, nr, nv, nb) / (fp32_peak * 1e12))
     ms_per_step = t_dev / args.steps * 1e3
@@ -487,7 +490,9 @@ def run_gpu(args, rank, world, w):
         "stage_share": stage_share,
         "step_roofline": {"t_roof_us": round(t_roof * 1e6, 2), "t_step_us": round(ms_per_step * 1e3, 2),
                           "frac": round(t_roof / (ms_per_step * 1e-3), 4),
-                          "definition": "max(compulsory bytes / measured HBM GB/s, algorithmic flops / FP32 SIMT peak)"},
+                          "definition": "max(compulsory bytes / measured HBM GB/s, algorithmic flops / measured FP32 FMA peak)",
+                          "fp32_tflops_measured": round(fp32_peak, 2), "fp32_tflops_derived": round(fp32_derived, 2),
+                          "fp64_tflops_measured": round(fp64_peak, 3)},
         "clocks": clocks,
         "steps_per_s": round(args.steps / t_dev, 2),
         "wall_s_timed_region": round(wall, 4),

@@ -210,7 +210,7 @@ typedef struct {
                           (32 values per thread, one shared-memory exchange per transform; FFT lengths
                           256 .. 2048, i.e. nfft/2 in 128 .. 1024; elsewhere 2 means 0).  Steps with
                           N-SGD or the causality mute run variant 0 whatever is set. */
-    int gemm_fwd;      /* MDC_GEMM_SIMT or MDC_GEMM_TC */
+    int gemm_fwd;      /* MDC_GEMM_SIMT, MDC_GEMM_TC or MDC_GEMM_GEMV */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
     int fft_prefetch;  /* 1: the update runs as persistent CTAs that prefetch the next tile's gradient
                           spectra while transforming the current one (variants 0 and 1, nfft <= 2048;
@@ -297,6 +297,15 @@ int mdc_plan_stage_times(mdc_plan_t plan, double *ms, long long *launches, int r
 const char *mdc_stage_name(int stage);
 /* Total kernel launches made by this plan since creation (host counter). */
 long long mdc_plan_launch_count(mdc_plan_t plan);
+
+/* Arithmetic-peak probe, for the roofline of the FP32 path.  Launches one kernel of `blocks` blocks of
+ * 256 threads on `stream` in which every thread runs 8 independent fused multiply-add chains for
+ * `iters` rounds (kind 0: FP32 fmaf, kind 1: FP64 fma) and writes one value to sink[thread]; the
+ * caller times the launch (CUDA events on `stream`) and divides *flops (host pointer, may be NULL;
+ * 2 flops per multiply-add) by the duration.  sink: device buffer of blocks * 256 elements of 4 bytes
+ * (kind 0) or 8 bytes (kind 1), owned by the caller.  iters must be a positive multiple of 16.
+ * Returns MDC_ERR_INVALID_ARG for a bad argument, MDC_ERR_CUDA if the launch fails. */
+int mdc_alu_probe(int kind, int blocks, int iters, void *sink, double *flops, void *stream);
 
 #ifdef __cplusplus
 }

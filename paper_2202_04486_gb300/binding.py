@@ -47,7 +47,7 @@ EXPORTED = (
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
     "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex", "smdd_lsqr", "mdc_plan_set_band",
-    "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy",
+    "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy", "mdc_alu_probe",
 )
 
 
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
     lib.mdc_batch_destroy.argtypes = [vp]
     lib.mdc_plan_launch_count.argtypes = [vp]
+    lib.mdc_alu_probe.argtypes = [i, i, i, vp, ctypes.POINTER(d), vp]
     lib.mdc_plan_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
         if name not in ("mdc_status_string", "mdc_stage_name", "mdc_plan_launch_count"):
@@ -257,6 +258,40 @@ def mdc_plan_stage_times(plan: int, reset: bool = False) -> dict:
 
 def mdc_plan_launch_count(plan: int) -> int:
     return int(load_library().mdc_plan_launch_count(ctypes.c_void_p(plan)))
+
+
+def mdc_alu_probe(kind: int, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launch the FMA throughput probe (kind 0 FP32, 1 FP64) on `stream`; returns its flop count."""
+    need = torch.float32 if kind == 0 else torch.float64
+    if sink.dtype != need or not sink.is_cuda or sink.numel() < blocks * 256:
+        raise MDCError(MDC_ERR_INVALID_ARG, "mdc_alu_probe")
+    fl = ctypes.c_double()
+    _check(load_library().mdc_alu_probe(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl),
+                                        _stream_ptr(stream)), "mdc_alu_probe")
+    return fl.value
+
+
+def alu_peak_tflops(kind: int = 0, iters: int | None = None, repeats: int = 5) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (median of `repeats` timed launches after
+    two warm-up launches; CUDA events on the launch stream).  Blocks: 8 per SM (64 warps per SM)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 8 * sms
+    if iters is None:
+        iters = 65536 if kind == 0 else 2048
+    sink = torch.empty(blocks * 256, device="cuda", dtype=torch.float32 if kind == 0 else torch.float64)
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        mdc_alu_probe(kind, blocks, iters, sink, st)
+    times = []
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        flops = mdc_alu_probe(kind, blocks, iters, sink, st)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    times.sort()
+    return flops / times[len(times) // 2] / 1e12
 
 
 def mdc_forward_static(D: torch.Tensor, X: torch.Tensor, idx: torch.Tensor, U: torch.Tensor, scale: float = 1.0,

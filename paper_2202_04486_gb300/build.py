@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsmdd_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "fft_kernels.cu", "gemm_kernels.cu", "setup_kernels.cu", "noalloc.cu", "gemm_tc.cu", "batch.cu", "lsqr.cu", "fft2_kernels.cu"]
+SOURCES = ["api.cu", "fft_kernels.cu", "gemm_kernels.cu", "setup_kernels.cu", "noalloc.cu", "gemm_tc.cu", "batch.cu", "lsqr.cu", "fft2_kernels.cu", "alu_probe.cu"]
 
 
 def _nvcc() -> str:

@@ -60,3 +60,12 @@ def test_null_arguments_rejected_without_touching_the_gpu(lib):
 def test_binding_fails_loudly_without_cuda():
     with pytest.raises(RuntimeError):
         binding.mdc_plan_create(torch.zeros(2, 2, 8), 2)
+
+
+def test_alu_probe_argument_errors_without_launching(lib):
+    import ctypes
+    d = ctypes.c_double()
+    assert lib.mdc_alu_probe(0, 1, 16, None, ctypes.byref(d), None) == binding.MDC_ERR_INVALID_ARG   # no sink
+    assert lib.mdc_alu_probe(2, 1, 16, None, None, None) == binding.MDC_ERR_INVALID_ARG              # unknown kind
+    assert lib.mdc_alu_probe(0, 1, 24, ctypes.c_void_p(16), None, None) == binding.MDC_ERR_INVALID_ARG  # iters % 16
+    assert lib.mdc_alu_probe(0, 0, 16, ctypes.c_void_p(16), None, None) == binding.MDC_ERR_INVALID_ARG  # no blocks
