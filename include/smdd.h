@@ -203,6 +203,10 @@ int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float 
                                 thread streams each gathered kernel row once.  Used where allowed: with
                                 a band limit, and for the adjoint with reciprocity, the call runs
                                 MDC_GEMM_SIMT instead. */
+#define MDC_GEMM_TC_STREAM 5 /* forward only: the split-BF16 tcgen05 product as a persistent kernel (one
+                                CTA per SM) fed by tiled copies of the tensor memory accelerator
+                                (MDC_PREC_BF16X3 plans only; MDC_ERR_UNSUPPORTED where the driver
+                                gives no tensor-map encoder) */
 
 typedef struct {
     int fft_variant;   /* 0: default radix order of the FFT plan; 1: the reversed order (accepted for
@@ -210,7 +214,7 @@ typedef struct {
                           (32 values per thread, one shared-memory exchange per transform; FFT lengths
                           256 .. 2048, i.e. nfft/2 in 128 .. 1024; elsewhere 2 means 0).  Steps with
                           N-SGD or the causality mute run variant 0 whatever is set. */
-    int gemm_fwd;      /* MDC_GEMM_SIMT, MDC_GEMM_TC or MDC_GEMM_GEMV */
+    int gemm_fwd;      /* MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_GEMV or MDC_GEMM_TC_STREAM */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
     int fft_prefetch;  /* 1: the update runs as persistent CTAs that prefetch the next tile's gradient
                           spectra while transforming the current one (variants 0 and 1, nfft <= 2048;

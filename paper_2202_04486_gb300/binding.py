@@ -41,6 +41,7 @@ MDC_GEMM_SIMT32 = 1
 MDC_GEMM_SIMT64 = 2
 MDC_GEMM_TC = 3
 MDC_GEMM_GEMV = 4
+MDC_GEMM_TC_STREAM = 5
 
 EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",

@@ -65,6 +65,8 @@ struct mdc_plan_s {
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
     int nf_active = 0;           // band limit of the products (0: every bin)
+    alignas(64) unsigned char xh_map[128] = {0};   // tensor map of Xh for the streamed forward product
+    bool xh_map_ok = false;
     LsqrWork *lsqr = nullptr;    // full-gradient solver workspace, allocated by the first smdd_lsqr
 };
 
@@ -184,6 +186,8 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.nf_active = p->nf_active;
     if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
+    if (p->gemm_fwd == MDC_GEMM_TC_STREAM && p->xh_map_ok)
+        return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd_stream(g, p->xh_map, p->nf, st); });
     if (p->gemm_fwd == MDC_GEMM_GEMV && gemv_supported(p->nv) && p->nf_active == 0)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_gemv_fwd(g, p->nf, st); });
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
@@ -387,6 +391,8 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     if (cudaMemsetAsync(p->Uh, 0, szU, st) != cudaSuccess) rc = MDC_ERR_CUDA;
     if (rc == MDC_OK && (fft_prepare(M) != cudaSuccess || gemm_prepare() != cudaSuccess)) rc = MDC_ERR_CUDA;
     if (rc == MDC_OK && precision == MDC_PREC_BF16X3 && tc_prepare() != cudaSuccess) rc = MDC_ERR_CUDA;
+    if (rc == MDC_OK && precision == MDC_PREC_BF16X3)   // without a map, MDC_GEMM_TC_STREAM is unsupported
+        p->xh_map_ok = tc_encode_fwd_map(p->xh_map, p->Xh, nr, nv, p->ldr, p->nf) == cudaSuccess;
     if (rc == MDC_OK) {
         // kernel spectra: D [ns][nr][nt] -> Dh [nf][ns][ldr] (same layout rule as the model)
         FftArgs a = base_fft(p);
@@ -634,13 +640,16 @@ int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
         if (cfg->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
     if (cfg->fft_variant < 0 || cfg->fft_variant > 2) return MDC_ERR_INVALID_ARG;
     if (cfg->fft_prefetch != 0 && cfg->fft_prefetch != 1) return MDC_ERR_INVALID_ARG;
-    if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC && cfg->gemm_fwd != MDC_GEMM_GEMV)
+    if (cfg->gemm_fwd != MDC_GEMM_SIMT && cfg->gemm_fwd != MDC_GEMM_TC && cfg->gemm_fwd != MDC_GEMM_GEMV &&
+        cfg->gemm_fwd != MDC_GEMM_TC_STREAM)
         return MDC_ERR_INVALID_ARG;
     if (cfg->gemm_adj < MDC_GEMM_SIMT || cfg->gemm_adj > MDC_GEMM_GEMV) return MDC_ERR_INVALID_ARG;
     if ((cfg->gemm_fwd == MDC_GEMM_GEMV || cfg->gemm_adj == MDC_GEMM_GEMV) && !gemv_supported(p->nv))
         return MDC_ERR_UNSUPPORTED;
-    if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_adj == MDC_GEMM_TC) && p->prec != MDC_PREC_BF16X3)
+    if ((cfg->gemm_fwd == MDC_GEMM_TC || cfg->gemm_fwd == MDC_GEMM_TC_STREAM || cfg->gemm_adj == MDC_GEMM_TC) &&
+        p->prec != MDC_PREC_BF16X3)
         return MDC_ERR_UNSUPPORTED;
+    if (cfg->gemm_fwd == MDC_GEMM_TC_STREAM && !p->xh_map_ok) return MDC_ERR_UNSUPPORTED;
     // the spectra a plan holds are the same for both radix orders: switching keeps them valid
     p->fft_variant = fft_has_variant(p->M, cfg->fft_variant) ? cfg->fft_variant : 0;
     p->fft_prefetch = (p->M <= 1024 && p->fft_variant != 2) ? cfg->fft_prefetch : 0;
@@ -745,9 +754,10 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
     }
     if (rc == MDC_OK) {
         double tbest = 1e300;
-        const int cand[3] = {MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_GEMV};
+        const int cand[4] = {MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_TC_STREAM, MDC_GEMM_GEMV};
         for (int c : cand) {
-            if (c == MDC_GEMM_TC && p->prec != MDC_PREC_BF16X3) continue;
+            if ((c == MDC_GEMM_TC || c == MDC_GEMM_TC_STREAM) && p->prec != MDC_PREC_BF16X3) continue;
+            if (c == MDC_GEMM_TC_STREAM && !p->xh_map_ok) continue;
             if (c == MDC_GEMM_GEMV && !gemv_supported(p->nv)) continue;
             p->gemm_fwd = c;
             const double t = time_it([&] { return gemm_forward(p, didx, nb, st); });

@@ -11,7 +11,12 @@
 // four BF16 planes (re hi, re lo, im hi, im lo) in the 128-byte swizzled layouts of tc_common.cuh;
 // thread 0 issues the MMAs and commits them to an mbarrier; every wait is bounded.  Status bits:
 // 1 = a source index out of range, 2 = a bounded wait gave up.
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "smdd_fft.cuh"
 #include "smdd_internal.h"
@@ -412,11 +417,238 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// forward, streamed: the product of k_tc_fwd by a persistent, warp-specialised kernel, one CTA per SM.
+// A CTA walks its tiles (f, 128 rows v, NB batch columns) chunk by chunk (64 of K = nr).
+//  * control warp (warp 16, one lane): issues four tiled copies of the tensor memory accelerator per
+//    chunk (boxes of 128 rows x 16 complex, 128-byte swizzled, zero-filled past nv and nr) into one of
+//    two staging buffers, and the MMAs of each half chunk (K = 32) once the split warps report its
+//    planes written;
+//  * split warps (0-15): convert the staged FP32 spectra and the gathered kernel rows (loaded into
+//    registers one chunk ahead) to the BF16 hi/lo planes, half by half, so the products of one half
+//    run while the other half is split; at the end of a tile they read the accumulators from TMEM and
+//    write the rows of C directly (16 consecutive complex per thread).
+// The warps meet only on mbarriers (full: copies landed; ready: planes of a half written, one arrive
+// per split warp; done: products of a half finished), every wait bounded.  Tiles are numbered
+// t = (f * gy + batch tile) * gx + v tile; the CTA takes t = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// tiles of bins above the band limit are zero-filled first.
+// ------------------------------------------------------------------------------------------------
+constexpr int TCS_SPLIT = 512;                 // split warps 0-15
+constexpr int TCS_THREADS = TCS_SPLIT + 32;    // + the control warp
+
+template <int NB>
+struct TcFwdS {
+    static constexpr int A_PLANE = 128 * 128;
+    static constexpr int B_PLANE = NB * 128;
+    static constexpr int PLANES = 4 * A_PLANE + 4 * B_PLANE;
+    static constexpr int BOX = 128 * 128;                  // one box: 128 rows x 16 complex FP32
+    static constexpr int STG = 4 * BOX;                    // one chunk
+    static constexpr size_t SMEM = PLANES + 2 * (size_t)STG + 1024;
+    static constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : 2 * NB;
+    static_assert(PLANES % 1024 == 0, "staging boxes must stay 1024-byte aligned");
+    static_assert(NB * 4 <= TCS_SPLIT, "one kernel-row unit per split thread and half chunk");
+};
+
+struct FwdTile {
+    int f, v0, b0;
+};
+template <int NB>
+__device__ __forceinline__ FwdTile fwd_tile(int t, int gx, int gy) {
+    const int vt = t % gx, r = t / gx;
+    return FwdTile{r / gy, vt * 128, (r % gy) * NB};
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int NB>
+__global__ void __launch_bounds__(TCS_THREADS, 1)
+    k_tc_fwd_stream(GemmArgs a, const __grid_constant__ CUtensorMap tmap, int gx, int gy, int n_active, int n_tiles) {
+    using G = TcFwdS<NB>;
+    extern __shared__ uint8_t tc_raw[];
+    __shared__ uint64_t full[2];    // copies into staging buffer 0 / 1 landed
+    __shared__ uint64_t ready[2];   // planes of half 0 / 1 written (one arrive per split warp)
+    __shared__ uint64_t done[2];    // products of half 0 / 1 finished
+    __shared__ uint32_t tmem_holder;
+    __shared__ int fail, s_issued, s_last[2];
+    uint8_t *planes = align1024(tc_raw);
+    uint8_t *stg0 = planes + G::PLANES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int t = n_active + blockIdx.x; t < n_tiles; t += gridDim.x) {   // above the band limit
+        const FwdTile T = fwd_tile<NB>(t, gx, gy);
+        zero_tile(a.C + (long long)T.f * a.sCf, a.ldb, T.v0, 128, T.b0, NB, a.nv, a.nb);
+    }
+    const int my_tiles = (int)blockIdx.x < n_active ? (n_active - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (my_tiles == 0) return;
+    const int nk = (a.nr + 63) / 64;
+    const int nchunks = my_tiles * nk;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&ready[i], TCS_SPLIT / 32);
+            mbar_init(&done[i], 1);
+        }
+        fail = 0;
+        s_issued = 0;
+        s_last[0] = s_last[1] = -1;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+
+    if (warp == TCS_SPLIT / 32) {
+        // ---------------- control warp ----------------
+        if (lane == 0) {
+            constexpr uint32_t idp = umma_idesc(128, NB, 0, 0, 0), idn = umma_idesc(128, NB, 0, 0, 1);
+            auto issue = [&](int g) {   // four boxes of chunk g into staging buffer g & 1
+                const FwdTile T = fwd_tile<NB>((int)blockIdx.x + (g / nk) * (int)gridDim.x, gx, gy);
+                const int k0 = (g % nk) * 64;
+                uint8_t *stg = stg0 + (g & 1) * G::STG;
+                mbar_arrive_expect_tx(&full[g & 1], (uint32_t)G::STG);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tma_load_3d(stg + j * G::BOX, &tmap, 2 * k0 + 32 * j, T.v0, T.f, &full[g & 1]);
+                s_issued = g + 1;
+            };
+            issue(0);
+            if (nchunks > 1) issue(1);
+            for (int g = 0; g < nchunks; ++g) {
+                const int kc = g % nk;
+                for (int h = 0; h < 2; ++h) {
+                    if (!mbar_wait_bounded(&ready[h], g & 1)) {
+                        fail = 1;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int k2 = 0; k2 < 2; ++k2) {
+                        const int ks = 2 * h + k2;
+                        uint64_t ad[4], bd[4];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            ad[p] = umma_desc(smem_u32(planes + p * G::A_PLANE + ks * 32), 16, 1024);
+                            bd[p] = umma_desc(smem_u32(planes + 4 * G::A_PLANE + p * G::B_PLANE + ks * 32), 16, 1024);
+                        }
+                        mma_complex_split(tmem, tmem + NB, ad, bd, idp, idn, (kc > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    umma_commit(&done[h]);
+                    s_last[h] = g;
+                }
+                if (*(volatile int *)&fail) break;
+                if (g + 2 < nchunks) issue(g + 2);   // staging buffer g & 1: both halves split
+            }
+        }
+    } else {
+        // ---------------- split warps ----------------
+        auto load_b = [&](int g, float2 (&zb)[2][8]) {
+            // thread u < 4 NB: kernel row u / 4, 8 complex at columns 8 (4h + u % 4) of halves h = 0, 1
+            // (an index out of range sets status bit 1 and gives a zero row)
+            if (tid >= NB * 4) return;
+            const FwdTile T = fwd_tile<NB>((int)blockIdx.x + (g / nk) * (int)gridDim.x, gx, gy);
+            const int k0 = (g % nk) * 64, row = tid >> 2, c = tid & 3, b = T.b0 + row;
+            const float2 *Df = a.Dh + (long long)T.f * a.sDf;
+            int s = -1;
+            if (b < a.nb) {
+                s = a.idx[b];
+                if (s < 0 || s >= a.ns) {
+                    atomicOr(a.status, 1);
+                    s = -1;
+                }
+            }
+            const float2 *rowp = s >= 0 ? Df + (long long)s * a.ldr : nullptr;
+            load8(rowp, k0 + 8 * c, a.nr, zb[0]);
+            load8(rowp, k0 + 32 + 8 * c, a.nr, zb[1]);
+        };
+        float2 zb[2][8];
+        load_b(0, zb);
+        for (int g = 0; g < nchunks; ++g) {
+            const int kc = g % nk;
+            const uint8_t *stg = stg0 + (g & 1) * G::STG;
+            if (!mbar_wait_bounded(&full[g & 1], (g >> 1) & 1)) fail = 1;   // chunk g staged
+            for (int h = 0; h < 2 && !*(volatile int *)&fail; ++h) {
+                if (g > 0 && !mbar_wait_bounded(&done[h], (g - 1) & 1)) {     // bytes of half h free
+                    fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                // units (row m, 8 complex c), c in 4h .. 4h+3: box c / 2, granules 4 (c % 2) .. +3 of
+                // the row, each stored at granule ^ (m % 8)
+                const int m = tid & 127, c = 4 * h + (tid >> 7);
+                const uint8_t *row = stg + (c >> 1) * G::BOX + m * 128;
+                float2 z[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 w = *reinterpret_cast<const float4 *>(row + (((4 * (c & 1) + j) ^ (m & 7)) << 4));
+                    z[2 * j] = make_float2(w.x, w.y);
+                    z[2 * j + 1] = make_float2(w.z, w.w);
+                }
+                store_planes(planes, m * 128 + ((c ^ (m & 7)) << 4), G::A_PLANE, split8(z, false));
+                if (tid < NB * 4) {
+                    const int brow = tid >> 2, bc = 4 * h + (tid & 3);
+                    store_planes(planes + 4 * G::A_PLANE, brow * 128 + ((bc ^ (brow & 7)) << 4), G::B_PLANE,
+                                 split8(zb[h], false));
+                }
+                fence_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ready[h]);
+            }
+            if (*(volatile int *)&fail) break;
+            if (g + 1 < nchunks) load_b(g + 1, zb);
+            if (kc == nk - 1) {
+                // the tile's epilogue: done[1] of this chunk follows every earlier product
+                if (!mbar_wait_bounded(&done[1], g & 1)) {
+                    fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const FwdTile T = fwd_tile<NB>((int)blockIdx.x + (g / nk) * (int)gridDim.x, gx, gy);
+                const int q = warp & 3, cc = warp >> 2;   // TMEM lanes 32q.., columns 16cc..
+                if (16 * cc < NB) {
+                    const int v = T.v0 + 32 * q + lane, c0 = 16 * cc;
+                    float re[16], im[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + c0, re);
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + NB + c0, im);
+                    if (v < a.nv) {
+                        float2 *Crow = a.C + (long long)T.f * a.sCf + (long long)v * a.ldb + T.b0 + c0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (T.b0 + c0 + j < a.nb) Crow[j] = make_float2(re[j], im[j]);
+                    }
+                }
+                tc_fence_before();   // the next tile's first products overwrite the accumulators
+            }
+        }
+    }
+    __syncthreads();
+    if (fail) {
+        // copies and products still in flight get one more bounded wait before the CTA frees TMEM
+        // and exits
+        if (tid == 0) {
+            for (int i = max(0, s_issued - 2); i < s_issued; ++i) mbar_wait_bounded(&full[i & 1], (i >> 1) & 1);
+            for (int h = 0; h < 2; ++h)
+                if (s_last[h] >= 0) mbar_wait_bounded(&done[h], s_last[h] & 1);
+            atomicOr(a.status, 2);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------------------------
 cudaError_t tc_prepare() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd<16, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd<32, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd<64, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<16>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<32>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<64>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     return cudaSuccess;
@@ -428,6 +660,47 @@ cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
     if (a.nb <= 16) k_tc_fwd<16, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16, S>::SMEM, st>>>(a);
     else if (a.nb <= 32) k_tc_fwd<32, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32, S>::SMEM, st>>>(a);
     else k_tc_fwd<64, S><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64, S>::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tensor map of the model spectra [nf][nv][ldr] complex, seen as FP32 [nf][nv][2 nr] (the padding
+// column of an odd nr lies outside it): boxes of 32 floats x 128 rows x 1 bin, 128-byte swizzle,
+// zero fill outside the tensor.  The encoder is taken from the driver at run time.
+cudaError_t tc_encode_fwd_map(void *map_out, const float2 *Xh, int nr, int nv, int ldr, int nf) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nr, (cuuint64_t)nv, (cuuint64_t)nf};
+    const cuuint64_t strides[2] = {(cuuint64_t)ldr * 8, (cuuint64_t)nv * ldr * 8};
+    const cuuint32_t box[3] = {32, 128, 1}, estr[3] = {1, 1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap *>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                              const_cast<float2 *>(Xh), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_fwd_stream(const GemmArgs &a, const void *map, int nf, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    CUtensorMap tmap;
+    memcpy(&tmap, map, sizeof(tmap));
+    const int gx = (a.nv + 127) / 128;
+    const int nb_tile = a.nb <= 16 ? 16 : a.nb <= 32 ? 32 : 64;
+    const int gy = (a.nb + nb_tile - 1) / nb_tile;
+    const int nf_act = (a.nf_active > 0 && a.nf_active < nf) ? a.nf_active : nf;
+    const int n_active = nf_act * gx * gy, n_tiles = nf * gx * gy;
+    const int grid = std::max(1, std::min(n_tiles, sms));
+    if (nb_tile == 16) k_tc_fwd_stream<16><<<grid, TCS_THREADS, TcFwdS<16>::SMEM, st>>>(a, tmap, gx, gy, n_active, n_tiles);
+    else if (nb_tile == 32) k_tc_fwd_stream<32><<<grid, TCS_THREADS, TcFwdS<32>::SMEM, st>>>(a, tmap, gx, gy, n_active, n_tiles);
+    else k_tc_fwd_stream<64><<<grid, TCS_THREADS, TcFwdS<64>::SMEM, st>>>(a, tmap, gx, gy, n_active, n_tiles);
     return cudaGetLastError();
 }
 

@@ -109,6 +109,10 @@ cudaError_t launch_gemv_adj(const GemmArgs &a, int nf, cudaStream_t st);
 // split-BF16 tensor-core products (tcgen05)
 cudaError_t tc_prepare();
 cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st);
+// streamed forward product fed by the tensor memory accelerator: map = 128-byte tensor map of the
+// model spectra written by tc_encode_fwd_map (64-byte aligned host memory)
+cudaError_t tc_encode_fwd_map(void *map_out, const float2 *Xh, int nr, int nv, int ldr, int nf);
+cudaError_t launch_tc_fwd_stream(const GemmArgs &a, const void *map, int nf, cudaStream_t st);
 cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
 
 // plan internals used by the batch runner (api.cu)

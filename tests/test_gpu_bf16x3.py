@@ -98,3 +98,51 @@ def test_bf16x3_dot_product():
     U = plan.forward(_cuda(X), ti).double().cpu().numpy()
     G = plan.adjoint(_cuda(Y), ti).double().cpu().numpy()
     assert abs(np.vdot(U, Y) - np.vdot(X, G)) <= 1e-4 * np.linalg.norm(U) * np.linalg.norm(Y)
+
+
+STREAM_SHAPES = SHAPES + [
+    (64, 301, 301, 40, 32),     # nr = 301: five K chunks, the last one 45 wide; v tail of 45 rows
+    (40, 20, 300, 90, 65),      # three v tiles, two batch tiles of 64 (the second with one column)
+    (24, 16, 16, 20, 1),        # batch of one
+]
+
+
+@pytest.mark.parametrize("shape", STREAM_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("band", [0, 5], ids=["full", "band5"])
+def test_streamed_forward_equals_tile_kernel(shape, band):
+    """MDC_GEMM_TC_STREAM (persistent, fed by tensor-memory-accelerator copies) splits the same values
+    and issues the same MMAs in the same order as MDC_GEMM_TC, so the two forward products agree bit for
+    bit; both meet the split-BF16 bar against the oracle (with a band limit, the oracle's band-limited
+    Tier B)."""
+    nt, nr, nv, ns, nb = shape
+    D, X, _, idx = _problem(nt, nr, nv, ns, nb, seed=7 * sum(shape) + band)
+    plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, precision=binding.MDC_PREC_BF16X3)
+    if band:
+        plan.set_band(band)
+    ti, Xg = _cuda(idx, torch.int32), _cuda(X)
+    plan.set_config(gemm_fwd=binding.MDC_GEMM_TC, gemm_adj=binding.MDC_GEMM_TC)
+    U_tile = plan.forward(Xg, ti).cpu().numpy()
+    plan.set_config(gemm_fwd=binding.MDC_GEMM_TC_STREAM, gemm_adj=binding.MDC_GEMM_TC)
+    U = plan.forward(Xg, ti).cpu().numpy()
+    assert plan.sync_status() == binding.MDC_OK
+    np.testing.assert_array_equal(U, U_tile)
+    ref = oracle.mdc_forward_fft(D, X, idx, band=band) if band else oracle.mdc_forward(D, X, idx)
+    _check(U, ref, f"U {shape}")
+
+
+def test_streamed_forward_reports_index_errors():
+    nt, nr, nv, ns, nb = 64, 40, 40, 30, 8
+    D, X, _, idx = _problem(nt, nr, nv, ns, nb, seed=11)
+    plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, precision=binding.MDC_PREC_BF16X3)
+    plan.set_config(gemm_fwd=binding.MDC_GEMM_TC_STREAM, gemm_adj=binding.MDC_GEMM_TC)
+    bad = idx.copy()
+    bad[3] = ns + 2
+    plan.forward(_cuda(X), _cuda(bad, torch.int32))
+    assert plan.sync_status() == binding.MDC_ERR_INDEX_RANGE
+    U = plan.forward(_cuda(X), _cuda(idx, torch.int32)).cpu().numpy()
+    assert plan.sync_status() == binding.MDC_OK
+    _check(U, oracle.mdc_forward(D, X, idx), "U after the error")
+    fp32 = binding.MDCPlan(_cuda(D), nv, nb_max=nb)
+    with pytest.raises(binding.MDCError) as e:
+        fp32.set_config(gemm_fwd=binding.MDC_GEMM_TC_STREAM)
+    assert e.value.status == binding.MDC_ERR_UNSUPPORTED
