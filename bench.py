@@ -391,42 +391,40 @@ def run_gpu(args, rank, world, w):
     flops = sum(step_flops(nt, nr, nv, len(batches[args.warmup + i])) for i in range(args.steps))
     losses = loss[: args.warmup + args.steps].cpu().numpy()
 
-    # e2e: the same steps with host inputs (pinned): batch index list and the batch rows of U_obs go
-    # host -> device every step, the loss comes back device -> host every step
+    # e2e: the same steps through smdd_step_host with host inputs: every step the plan copies the batch
+    # index list and the batch rows of U_obs (pinned) host -> device on its copy stream, overlapping the
+    # previous step, and the step's loss comes back device -> host (pinned); the host reads the loss of
+    # step k - 1 once step k is queued, and the last one after the loop
     U_host = U_obs.cpu().pin_memory()
     Xe = torch.zeros_like(X)
-    Ub = torch.empty((nb, nv, nt), device=dev)
-    idx_host = [torch.from_numpy(b).pin_memory() for b in batches]
-    idx_buf = torch.empty(nb, dtype=torch.int32, device=dev)
-    loss_dev = torch.zeros((), device=dev, dtype=torch.float64)
-    loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
+    idx_host = [torch.from_numpy(np.ascontiguousarray(b, dtype=np.int32)) for b in batches]
+    loss_host = torch.zeros(len(batches), dtype=torch.float64).pin_memory()
     h2d = d2h = 0
 
-    def e2e_step(k, count):
+    def e2e_run(ks, count):
         nonlocal h2d, d2h
-        ih = idx_host[k]
-        n = ih.numel()
-        ib = idx_buf[:n]
-        ib.copy_(ih, non_blocking=True)
-        for b in range(n):
-            Ub[b].copy_(U_host[int(ih[b])], non_blocking=True)
-        fl = flags | binding.SMDD_UOBS_GATHERED | (binding.SMDD_REUSE_XHAT if k > 0 else 0)
-        binding.smdd_step(plan.handle, Xe, Ub[:n], ib, alpha, fl, loss_dev)
-        loss_host.copy_(loss_dev, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        _ = float(loss_host)
-        if count:
-            h2d += ih.numel() * 4 + n * nv * nt * 4
-            d2h += 8
+        done = []
+        for j, k in enumerate(ks):
+            fl = flags | (binding.SMDD_REUSE_XHAT if k > 0 else 0)
+            binding.smdd_step_host(plan.handle, Xe, U_host, idx_host[k], alpha, fl, loss_host[k:k + 1], stream)
+            e = torch.cuda.Event()
+            e.record(stream)
+            done.append(e)
+            if j > 0:
+                done[j - 1].synchronize()
+                _ = float(loss_host[ks[j - 1]])
+            if count:
+                h2d += idx_host[k].numel() * 4 + idx_host[k].numel() * nv * nt * 4
+                d2h += 8
+        done[-1].synchronize()
+        _ = float(loss_host[ks[-1]])
 
-    for k in range(args.warmup):
-        e2e_step(k, False)
+    e2e_run(list(range(args.warmup)), False)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for i in range(args.steps):
-        e2e_step(args.warmup + i, True)
+    e2e_run([args.warmup + i for i in range(args.steps)], True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - e0
 

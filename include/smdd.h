@@ -128,6 +128,22 @@ typedef struct {
 int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
               const smdd_params *params, double *loss, void *stream);
 
+/* smdd_step_host: the step of smdd_step with the batch taken from host memory (a data-loader step).
+ *   U_obs_host : [ns][nv][nt] host float32 (pinned, for the copies to be asynchronous).
+ *   idx_host   : host int32[nb]; checked on the host (MDC_ERR_INDEX_RANGE before anything is queued)
+ *                and copied at once, so the caller may reuse it when the call returns.
+ *   loss_host  : host float64 written asynchronously with 1/2 ||R||^2 (pinned memory; valid once
+ *                `stream` has passed the step), or NULL.
+ *   flags      : SMDD_RECIPROCITY, SMDD_KEEP_XHAT, SMDD_REUSE_XHAT.
+ * The plan copies the index list and the nb rows U_obs_host[idx[b]] (consecutive sources as one copy)
+ * into one of two device staging slots on a copy stream of its own, then queues the step on `stream`
+ * behind them: the copies of a call overlap the step of the previous call, and a slot is refilled only
+ * after the step two calls back has finished with it.  The rows of U_obs_host must stay unchanged until
+ * the step has run.  The staging slots (2 nb_max nv nt floats) are allocated by the first call
+ * (MDC_ERR_OOM if that fails). */
+int smdd_step_host(mdc_plan_t plan, float *X, const float *U_obs_host, const int32_t *idx_host, int nb,
+                   const smdd_params *params, double *loss_host, void *stream);
+
 /* smdd_step_ex: the same step with the N-SGD solver and the causality preconditioner.
  * N-SGD is SGD with Nesterov momentum in the form of Sutskever et al. (2013) -- the solver the paper
  * reports as converging fastest -- written on the look-ahead point: with g the preconditioned batch

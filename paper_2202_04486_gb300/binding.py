@@ -49,6 +49,7 @@ EXPORTED = (
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
     "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex", "smdd_lsqr", "mdc_plan_set_band",
     "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy", "mdc_alu_probe",
+    "smdd_step_host",
 )
 
 
@@ -122,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_batch_destroy.argtypes = [vp]
     lib.mdc_plan_launch_count.argtypes = [vp]
     lib.mdc_alu_probe.argtypes = [i, i, i, vp, ctypes.POINTER(d), vp]
+    lib.smdd_step_host.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(smdd_params), vp, vp]
     lib.mdc_plan_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
         if name not in ("mdc_status_string", "mdc_stage_name", "mdc_plan_launch_count"):
@@ -216,6 +218,29 @@ def smdd_step(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor
     _check(load_library().smdd_step(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
                                     _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
                                     ctypes.byref(p), lp, _stream_ptr(stream)), "smdd_step")
+
+
+def _host(t: torch.Tensor, name: str, dtype) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def smdd_step_host(plan: int, X: torch.Tensor, U_obs_host: torch.Tensor, idx_host: torch.Tensor, alpha: float,
+                   flags: int = 0, loss_host: torch.Tensor | None = None, stream=None) -> None:
+    """SGD step with the batch taken from host memory: U_obs_host [ns][nv][nt] float32 (pinned for
+    asynchronous copies), idx_host int32 [nb] (CPU), loss_host a CPU float64 tensor whose first element
+    receives 1/2 ||R||^2 once the stream has run the step (pinned for an asynchronous copy), or None."""
+    p = smdd_params(float(alpha), int(flags))
+    lp = ctypes.c_void_p(0) if loss_host is None else _host(loss_host, "loss_host", torch.float64)
+    _check(load_library().smdd_step_host(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
+                                         _host(U_obs_host, "U_obs_host", torch.float32),
+                                         _host(idx_host, "idx_host", torch.int32), idx_host.numel(), ctypes.byref(p), lp,
+                                         _stream_ptr(stream)), "smdd_step_host")
 
 
 def smdd_step_ex(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor, alpha: float, flags: int = 0,

@@ -65,6 +65,17 @@ struct mdc_plan_s {
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
     int nf_active = 0;           // band limit of the products (0: every bin)
+    // host-input steps (smdd_step_host): two device staging slots, filled on a copy stream
+    struct HostStage {
+        float *U[2] = {nullptr, nullptr};              // [nbmax][nv][nt] batch rows
+        int32_t *idx[2] = {nullptr, nullptr};          // [nbmax] batch indices (device)
+        int32_t *idx_pinned[2] = {nullptr, nullptr};   // [nbmax] batch indices (pinned host copy)
+        double *loss[2] = {nullptr, nullptr};
+        cudaEvent_t copied[2] = {nullptr, nullptr};    // the slot's copies landed
+        cudaEvent_t consumed[2] = {nullptr, nullptr};  // the slot's step finished with it
+        cudaStream_t copy = nullptr;
+        int next = 0;
+    } *hs = nullptr;
     alignas(64) unsigned char xh_map[128] = {0};   // tensor map of Xh for the streamed forward product
     bool xh_map_ok = false;
     LsqrWork *lsqr = nullptr;    // full-gradient solver workspace, allocated by the first smdd_lsqr
@@ -414,10 +425,47 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     return MDC_OK;
 }
 
+static void host_stage_free(mdc_plan_s *p) {
+    if (!p->hs) return;
+    auto &h = *p->hs;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h.U[i]);
+        cudaFree(h.idx[i]);
+        cudaFree(h.loss[i]);
+        cudaFreeHost(h.idx_pinned[i]);
+        if (h.copied[i]) cudaEventDestroy(h.copied[i]);
+        if (h.consumed[i]) cudaEventDestroy(h.consumed[i]);
+    }
+    if (h.copy) cudaStreamDestroy(h.copy);
+    delete p->hs;
+    p->hs = nullptr;
+}
+
+static int host_stage_init(mdc_plan_s *p) {
+    p->hs = new mdc_plan_s::HostStage;
+    auto &h = *p->hs;
+    bool ok = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < 2; ++i) {
+        ok = cudaMalloc(&h.U[i], (size_t)p->nbmax * p->nv * p->nt * sizeof(float)) == cudaSuccess &&
+             cudaMalloc(&h.idx[i], (size_t)p->nbmax * sizeof(int32_t)) == cudaSuccess &&
+             cudaMalloc(&h.loss[i], sizeof(double)) == cudaSuccess &&
+             cudaHostAlloc(&h.idx_pinned[i], (size_t)p->nbmax * sizeof(int32_t), cudaHostAllocDefault) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h.copied[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h.consumed[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        host_stage_free(p);
+        return MDC_ERR_OOM;
+    }
+    return MDC_OK;
+}
+
 int mdc_plan_destroy(mdc_plan_t p) {
     if (!p) return MDC_OK;
     DeviceGuard dg(p->device);
     cudaDeviceSynchronize();
+    host_stage_free(p);
     cudaFree(p->Dh);
     cudaFree(p->Xh);
     cudaFree(p->Uh);
@@ -593,6 +641,53 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
     if ((flags & SMDD_RECIPROCITY) && p->nr != p->nv) return MDC_ERR_SHAPE;
     DeviceGuard dg(p->device);
     return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags, nullptr, 0.f, nullptr, loss, (cudaStream_t)stream);
+}
+
+int smdd_step_host(mdc_plan_t p, float *X, const float *U_host, const int32_t *idx_host, int nb,
+                   const smdd_params *prm, double *loss_host, void *stream) {
+    int rc = check_common(p, X, U_host, idx_host, nb);
+    if (rc) return rc;
+    if (!prm) return MDC_ERR_INVALID_ARG;
+    const int flags = prm->flags;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT)) return MDC_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
+    if ((flags & SMDD_RECIPROCITY) && p->nr != p->nv) return MDC_ERR_SHAPE;
+    for (int b = 0; b < nb; ++b)
+        if (idx_host[b] < 0 || idx_host[b] >= p->ns) return MDC_ERR_INDEX_RANGE;
+    DeviceGuard dg(p->device);
+    if (!p->hs && (rc = host_stage_init(p))) return rc;
+    auto &h = *p->hs;
+    const int s = h.next;
+    h.next ^= 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the pinned index slot was the source of this slot's previous copy (long finished in a pipeline)
+    if (cudaEventSynchronize(h.copied[s]) != cudaSuccess) return MDC_ERR_CUDA;
+    memcpy(h.idx_pinned[s], idx_host, (size_t)nb * sizeof(int32_t));
+    // the device slot is free once the step that used it two calls back has finished
+    if (cudaStreamWaitEvent(h.copy, h.consumed[s], 0) != cudaSuccess) return MDC_ERR_CUDA;
+    if (cudaMemcpyAsync(h.idx[s], h.idx_pinned[s], (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice, h.copy) !=
+        cudaSuccess)
+        return MDC_ERR_CUDA;
+    const size_t row = (size_t)p->nv * p->nt;
+    for (int b = 0; b < nb;) {
+        int e = b + 1;
+        while (e < nb && idx_host[e] == idx_host[e - 1] + 1) ++e;   // consecutive sources: one copy
+        if (cudaMemcpyAsync(h.U[s] + (size_t)b * row, U_host + (size_t)idx_host[b] * row, (size_t)(e - b) * row * sizeof(float),
+                            cudaMemcpyHostToDevice, h.copy) != cudaSuccess)
+            return MDC_ERR_CUDA;
+        b = e;
+    }
+    if (cudaEventRecord(h.copied[s], h.copy) != cudaSuccess || cudaStreamWaitEvent(st, h.copied[s], 0) != cudaSuccess)
+        return MDC_ERR_CUDA;
+    rc = step_impl(p, X, h.U[s], h.idx[s], nb, prm->alpha, flags | SMDD_UOBS_GATHERED, nullptr, 0.f, nullptr,
+                   loss_host ? h.loss[s] : nullptr, st);
+    if (rc) return rc;
+    if (loss_host && cudaMemcpyAsync(loss_host, h.loss[s], sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return MDC_ERR_CUDA;
+    if (cudaEventRecord(h.consumed[s], st) != cudaSuccess) return MDC_ERR_CUDA;
+    return MDC_OK;
 }
 
 int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb,

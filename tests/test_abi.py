@@ -69,3 +69,7 @@ def test_alu_probe_argument_errors_without_launching(lib):
     assert lib.mdc_alu_probe(2, 1, 16, None, None, None) == binding.MDC_ERR_INVALID_ARG              # unknown kind
     assert lib.mdc_alu_probe(0, 1, 24, ctypes.c_void_p(16), None, None) == binding.MDC_ERR_INVALID_ARG  # iters % 16
     assert lib.mdc_alu_probe(0, 0, 16, ctypes.c_void_p(16), None, None) == binding.MDC_ERR_INVALID_ARG  # no blocks
+
+
+def test_host_step_argument_errors_without_launching(lib):
+    assert lib.smdd_step_host(None, None, None, None, 1, None, None, None) == binding.MDC_ERR_INVALID_ARG
