@@ -683,11 +683,12 @@ int smdd_step_host(mdc_plan_t p, float *X, const float *U_host, const int32_t *i
         return MDC_ERR_CUDA;
     rc = step_impl(p, X, h.U[s], h.idx[s], nb, prm->alpha, flags | SMDD_UOBS_GATHERED, nullptr, 0.f, nullptr,
                    loss_host ? h.loss[s] : nullptr, st);
-    if (rc) return rc;
-    if (loss_host && cudaMemcpyAsync(loss_host, h.loss[s], sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return MDC_ERR_CUDA;
-    if (cudaEventRecord(h.consumed[s], st) != cudaSuccess) return MDC_ERR_CUDA;
-    return MDC_OK;
+    if (rc == MDC_OK && loss_host &&
+        cudaMemcpyAsync(loss_host, h.loss[s], sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = MDC_ERR_CUDA;
+    // recorded on failure too: whatever part of the step was queued still reads this slot
+    if (cudaEventRecord(h.consumed[s], st) != cudaSuccess && rc == MDC_OK) rc = MDC_ERR_CUDA;
+    return rc;
 }
 
 int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb,
