@@ -1,16 +1,25 @@
-"""Benchmark of the stochastic MDD hot path: one SGD step (forward MDC on a source batch, residual,
-adjoint, reciprocity-preconditioned update) per timed iteration, on synthetic data shaped like the
-paper's workloads.
+"""Benchmark of the stochastic MDD hot path: SGD steps (forward MDC on a source batch, residual, adjoint,
+update) on synthetic data shaped like the paper's workloads.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
 
-Prints one JSON line (rank 0).  `value` is the algorithmic FLOP rate of the whole job:
-F_step = 16 nb nr nv nf (forward + adjoint complex products, 8 real flops per complex MAC)
-       + 5 nfft log2(nfft) (nr nv + nb nv) (two real FFTs per model trace and per residual trace,
-         2.5 N log2 N flops each), summed over the steps of all ranks, divided by the max over ranks of
-the device time of the K timed steps.  L2 is flushed (256 MiB write, outside the per-step CUDA events)
-before every timed step; --l2 none / auto run the steps back to back (auto: when a step's own HBM traffic
-exceeds four times the L2 size), which measured within 0.5 % of the flushed steps on the default workload.
+Default workload: 48 independent MDD problems of uneven sizes (nr, nv in [64, 600], ns in [64, 800], nt in
+{256, 512, 1024, 1500}, the largest member nt = 1500 with nr = nv = ns = 1200), batch 32, split-BF16
+tensor-core products; a step of this line is one epoch of every member, replayed from one captured CUDA
+graph.  Single problems: --workload smdd_nt512_n201_nb16_recip etc.
+
+Prints one JSON line (rank 0).  `value` is the algorithmic FLOP rate of the whole job: per SGD step
+    F_gemm = 16 nb nr nv nf                      (forward + adjoint complex products, 8 real flops / MAC)
+    F_fft  = 5 N log2(N) (nr nv + nb nv)         (two real FFTs per model trace and per residual trace,
+                                                  2.5 N log2 N flops each)
+with N the smallest 2^a 3^b 5^c >= 2 nt - 1 and nf = N/2 + 1 (the shortest transform that keeps the
+linear convolution exact, whatever length the library pads to), summed over the steps of all ranks and
+divided by the max over ranks of the device time.  The roofline figures divide the same algorithmic work
+by the measured peaks: compulsory bytes (the model read and written, the gathered kernel spectra, the
+observed rows of the batch) over the measured HBM copy bandwidth, FFT flops over the measured FP32 FMA
+rate, product flops over the FP32 rate (FP32 products) or the sustained BF16 tensor rate (split-BF16
+products).  Bytes a staged pipeline moves in addition (the model and gradient spectra written by one
+kernel and read by the next) are reported per kernel as `staged_bytes`, not counted as algorithmic.
 
 --impl reference times the FP64 oracle (direct time-domain sums, OpenMP on the host cores) on a bounded
 sample of each step (a subset of virtual-source columns; forward and adjoint cost are linear in the
@@ -37,56 +46,77 @@ sys.path.insert(0, ROOT)
 
 from paper_2202_04486_gb300 import synth  # noqa: E402
 
-DEFAULT_WORKLOAD = "smdd_nt512_n201_nb16_recip"
+BATCH_WORKLOAD = "smdd_batch48_nb32"
+DEFAULT_WORKLOAD = BATCH_WORKLOAD
+DEFAULT_PRECISION = "bf16x3"
+FIXED_ERROR_WORKLOADS = ("smdd_nt1024_n301_ns401_nb32", "smdd_nt1024_n301_ns401_nb64")
 METRIC = "MDC fwd+adj GFLOP/s (SMDD step)"
 UNIT = "GFLOP/s"
 
 
 # ------------------------------------------------------------------------------------------------
-# work model
+# work model (algorithmic)
 # ------------------------------------------------------------------------------------------------
 def nfft_for(nt: int) -> int:
-    n = 64
-    while n < 2 * nt - 1:
-        n *= 2
-    return n
-
-
-def step_flops(nt, nr, nv, nb) -> float:
-    nfft = nfft_for(nt)
-    nf = nfft // 2 + 1
-    return 16.0 * nb * nr * nv * nf + 5.0 * nfft * math.log2(nfft) * (nr * nv + nb * nv)
+    """Smallest 2^a 3^b 5^c >= 2 nt - 1: the shortest FFT whose circular convolution equals the linear
+    one on [0, nt) (the algorithmic length; the library may pad further)."""
+    n = max(2 * nt - 1, 1)
+    while True:
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return n
+        n += 1
 
 
 def nf_of(nt: int) -> int:
     return nfft_for(nt) // 2 + 1
 
 
+def fft_flops(nt: int) -> float:
+    """2.5 N log2 N for one real FFT of the algorithmic length N."""
+    n = nfft_for(nt)
+    return 2.5 * n * math.log2(n)
+
+
+def step_work(nt, nr, nv, nb) -> tuple[float, float]:
+    """(F_gemm, F_fft) of one SGD step."""
+    return 16.0 * nb * nr * nv * nf_of(nt), 2.0 * fft_flops(nt) * (nr * nv + nb * nv)
+
+
+def step_flops(nt, nr, nv, nb) -> float:
+    return sum(step_work(nt, nr, nv, nb))
+
+
 def step_bytes_compulsory(nt, nr, nv, nb, recip) -> float:
-    nfft = nfft_for(nt)
-    nf = nfft // 2 + 1
-    b = 2 * nr * nv * nt * 4 + nf * nb * nr * 8 + nb * nv * nt * 4
+    """Model read + write, the gathered kernel spectra, the batch rows of U_obs (and, with reciprocity,
+    the round trip of the gradient that couples trace (r, v) with (v, r))."""
+    b = 2 * nr * nv * nt * 4 + nf_of(nt) * nb * nr * 8 + nb * nv * nt * 4
     if recip:
         b += 2 * nr * nv * nt * 4
     return float(b)
 
 
 def kernel_work(stage, nt, nr, nv, nb):
-    """Algorithmic bytes and flops of one launch of a stage (see the design notes for the derivation)."""
-    nfft = nfft_for(nt)
-    nf = nfft // 2 + 1
-    fft_flops = 2.5 * nfft * math.log2(nfft)
-    if stage == "update":      # read Gh, read X, write X, write Xh (fused re-transform)
-        return dict(bytes=nv * nr * (2 * nf * 8 + 2 * nt * 4), flops=2 * fft_flops * nv * nr)
-    if stage == "cgemm_fwd":   # read Xh, gathered kernel rows, write Uh
-        return dict(bytes=nf * (nv * nr + nb * nr + nv * nb) * 8, flops=8.0 * nv * nr * nb * nf)
-    if stage == "cgemm_adj":   # read Rh, gathered kernel rows, write Gh
-        return dict(bytes=nf * (nv * nb + nb * nr + nv * nr) * 8, flops=8.0 * nv * nr * nb * nf)
-    if stage == "residual":    # read Uh, read U_obs rows, write Rh
-        return dict(bytes=nb * nv * (2 * nf * 8 + nt * 4), flops=2 * fft_flops * nb * nv)
-    if stage == "rfft":        # read X, write Xh
-        return dict(bytes=nv * nr * (nt * 4 + nf * 8), flops=fft_flops * nv * nr)
-    return dict(bytes=0, flops=0)
+    """Algorithmic bytes and flops of one launch of a stage, and the bytes the staged pipeline moves in
+    addition (spectra written by one kernel and read by the next), at the algorithmic FFT length."""
+    nf = nf_of(nt)
+    ff = fft_flops(nt)
+    if stage == "update":      # inverse FFT of the gradient, update, FFT of the new model, per model trace
+        return dict(bytes=2 * nv * nr * nt * 4, flops=2 * ff * nv * nr, staged=2 * nv * nr * nf * 8, tensor=False)
+    if stage == "cgemm_fwd":   # products with the gathered kernel rows; model spectra in, batch spectra out
+        return dict(bytes=nf * nb * nr * 8, flops=8.0 * nv * nr * nb * nf, staged=nf * (nv * nr + nv * nb) * 8,
+                    tensor=True)
+    if stage == "cgemm_adj":   # residual spectra and gathered kernel rows in, gradient spectra out
+        return dict(bytes=nf * nb * nr * 8, flops=8.0 * nv * nr * nb * nf, staged=nf * (nv * nb + nv * nr) * 8,
+                    tensor=True)
+    if stage == "residual":    # inverse FFT, window, subtraction of the observed rows, loss, FFT
+        return dict(bytes=nb * nv * nt * 4, flops=2 * ff * nb * nv, staged=2 * nb * nv * nf * 8, tensor=False)
+    if stage == "rfft":        # model spectra of the first step
+        return dict(bytes=nv * nr * nt * 4, flops=ff * nv * nr, staged=nv * nr * nf * 8, tensor=False)
+    return dict(bytes=0, flops=0, staged=0, tensor=False)
 
 
 def load_peaks():
@@ -95,12 +125,56 @@ def load_peaks():
         with open(path) as f:
             pk = json.load(f)
         return pk, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
     """FP32 SIMT peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class Peaks:
+    """The roofline denominators: HBM copy bandwidth and sustained BF16 tensor rate from
+    MEASURED_PEAKS.json, FP32 FMA rate measured in this run by the library's probe."""
+
+    def __init__(self, fp32_tflops: float, fp32_derived: float):
+        pk, src = load_peaks()
+        self.hbm = float(pk["hbm_gbs"]) * 1e9
+        self.bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))) * 1e12
+        self.fp32 = fp32_tflops * 1e12
+        self.fp32_derived = fp32_derived
+        self.source = src
+
+    def kernel_roof(self, stage, work, ms, tensor_products: bool):
+        """Roofline of one launch: T_roof = max(bytes / HBM, flops / arithmetic peak); the binding resource
+        names the bound; frac = T_roof / measured duration (= achieved / peak in the binding unit)."""
+        t = ms * 1e-3
+        on_tc = work["tensor"] and tensor_products
+        p_ar = self.bf16 if on_tc else self.fp32
+        t_mem, t_ar = work["bytes"] / self.hbm, work["flops"] / p_ar
+        if t_mem >= t_ar:
+            roof = {"bound": "hbm", "achieved": round(work["bytes"] / t / 1e9, 1), "peak": round(self.hbm / 1e9, 1),
+                    "unit": "GB/s", "peak_source": f"{self.source} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        else:
+            roof = {"bound": "tensor" if on_tc else "alu", "achieved": round(work["flops"] / t / 1e12, 3),
+                    "peak": round(p_ar / 1e12, 2), "unit": "TFLOP/s",
+                    "peak_source": ("sustained BF16 dense tensor rate (MEASURED_PEAKS.json bf16_tflops_sustained); "
+                                    "algorithmic complex-product flops, not the split products" if on_tc else
+                                    "FP32 FMA rate measured in this run (mdc_alu_probe)")}
+        roof["frac"] = round(max(t_mem, t_ar) / t, 4)
+        roof["kernel"] = stage
+        roof["launch_ms"] = round(ms, 5)
+        roof["algorithmic_bytes"] = int(work["bytes"])
+        roof["algorithmic_flops"] = float(work["flops"])
+        roof["staged_bytes"] = int(work["staged"])
+        roof["staged_gbs"] = round((work["bytes"] + work["staged"]) / t / 1e9, 1)
+        return roof
+
+    def step_roof_s(self, nt, nr, nv, nb, recip, tensor_products: bool) -> float:
+        """T_roof of one step: max(B / HBM, F_gemm / P_gemm + F_fft / P_FP32)."""
+        fg, ff = step_work(nt, nr, nv, nb)
+        p_gemm = self.bf16 if tensor_products else self.fp32
+        return max(step_bytes_compulsory(nt, nr, nv, nb, recip) / self.hbm, fg / p_gemm + ff / self.fp32)
 
 
 def kernel_source_hash() -> str:
@@ -297,6 +371,33 @@ def oracle_extra(w, D, X, U_obs, idx, target_s=3.0):
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
+def measured_peaks(dev):
+    """FP32 FMA rate measured now by the library's probe (and the lane-count figure beside it)."""
+    import torch
+
+    from paper_2202_04486_gb300 import binding
+
+    props = torch.cuda.get_device_properties(dev)
+    pk, _ = load_peaks()
+    fp32_derived = fp32_alu_peak_tflops(props.multi_processor_count, pk.get("sm_max_mhz", 2070.0))
+    return Peaks(binding.alu_peak_tflops(0), fp32_derived), binding.alu_peak_tflops(1)
+
+
+def stage_roofs(peaks, stage, member, tensor_products):
+    """Per-stage roofline of the timed steps: stage -> (ms, launches) from the library's stage timers."""
+    nt, nr, nv, nb = member
+    out = {}
+    for k, (ms, n) in stage.items():
+        if n <= 0 or k not in ("rfft", "cgemm_fwd", "residual", "cgemm_adj", "update"):
+            continue
+        out[k] = peaks.kernel_roof(k, kernel_work(k, nt, nr, nv, nb), ms / n, tensor_products)
+        out[k]["launches"] = int(n)
+    tot = sum(v["launch_ms"] * v["launches"] for v in out.values())
+    for v in out.values():
+        v["share"] = round(v["launch_ms"] * v["launches"] / tot, 4)
+    return out
+
+
 def run_gpu(args, rank, world, w):
     import torch
 
@@ -323,23 +424,23 @@ def run_gpu(args, rank, world, w):
         rms = U_obs.pow(2).mean().sqrt()
         U_obs += w["noise"] * rms * torch.from_numpy(p.noise.astype(np.float32)).to(dev)
     gen.close()
-    if args.fixed_error_epochs <= 0 and args.solver_epochs <= 0:
-        del X_true
 
-    prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
+    tc = args.precision == "bf16x3"
+    prec = binding.MDC_PREC_BF16X3 if tc else binding.MDC_PREC_FP32
     plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
     chosen = plan.autotune(nb, binding.SMDD_RECIPROCITY if recip else 0, reps=5) if args.autotune else plan.get_config()
     sigma2 = plan.sigma2_max(60)
     alpha = 0.5 * 2.0 / sigma2
     flags = (binding.SMDD_RECIPROCITY if recip else 0) | binding.SMDD_KEEP_XHAT
     X = torch.zeros((nv, nr, nt), device=dev)
-    n_ep = (args.warmup + args.steps) // math.ceil(ns / nb) + 2
+    n_ep = 2 * (args.warmup + args.steps) // math.ceil(ns / nb) + 3
     batches = [b for ep in synth.epoch_batches(ns, nb, n_ep, seed=rank) for b in ep]
     idx_dev = [torch.from_numpy(b).to(dev) for b in batches]
     loss = torch.zeros(len(batches), device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
-    # L2 policy: flush before every timed step unless the step's own traffic is far larger than L2
-    # (then back-to-back steps, as an SGD run issues them, and the inputs themselves evict L2)
+    # L2 policy (the same for the device-timed and the end-to-end loop): flush before every timed step
+    # unless the step's own traffic is far larger than L2 (then back-to-back steps, as an SGD run issues
+    # them, and the inputs themselves evict L2)
     l2_bytes = 126 * 1024 * 1024
     step_traffic = step_bytes_compulsory(nt, nr, nv, nb, recip) + 4.0 * nf_of(nt) * nv * nr * 8
     do_flush = args.l2 == "flush" or (args.l2 == "auto" and step_traffic < 4 * l2_bytes)
@@ -355,9 +456,7 @@ def run_gpu(args, rank, world, w):
         one_step(k)
     torch.cuda.synchronize()
 
-    # timed region: K steps, L2 flushed before each, per-step CUDA events on the launching stream
-    binding.mdc_plan_set_profiling(plan.handle, True)
-    binding.mdc_plan_stage_times(plan.handle, reset=True)
+    # timed region: K steps, per-step CUDA events on the launching stream, stage timers off
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     l0 = binding.mdc_plan_launch_count(plan.handle)
     if world > 1:
@@ -381,8 +480,6 @@ def run_gpu(args, rank, world, w):
     if world > 1:
         torch.distributed.barrier()
     launches = binding.mdc_plan_launch_count(plan.handle) - l0
-    stage = binding.mdc_plan_stage_times(plan.handle, reset=True)
-    binding.mdc_plan_set_profiling(plan.handle, False)
     status = plan.sync_status()
     if status != binding.MDC_OK:
         raise RuntimeError(f"device status {binding.status_string(status)}")
@@ -391,10 +488,22 @@ def run_gpu(args, rank, world, w):
     flops = sum(step_flops(nt, nr, nv, len(batches[args.warmup + i])) for i in range(args.steps))
     losses = loss[: args.warmup + args.steps].cpu().numpy()
 
+    # stage shares: the same steps once more with the library's per-kernel CUDA events (outside the timed
+    # region, same L2 policy)
+    binding.mdc_plan_set_profiling(plan.handle, True)
+    binding.mdc_plan_stage_times(plan.handle, reset=True)
+    for i in range(args.steps):
+        k = args.warmup + args.steps + i
+        if do_flush:
+            flush.fill_(float(k))
+        one_step(k)
+    stage = binding.mdc_plan_stage_times(plan.handle, reset=True)
+    binding.mdc_plan_set_profiling(plan.handle, False)
+
     # e2e: the same steps through smdd_step_host with host inputs: every step the plan copies the batch
     # index list and the batch rows of U_obs (pinned) host -> device on its copy stream, overlapping the
     # previous step, and the step's loss comes back device -> host (pinned); the host reads the loss of
-    # step k - 1 once step k is queued, and the last one after the loop
+    # step k - 1 once step k is queued, and the last one after the loop.  Same L2 policy as above.
     U_host = U_obs.cpu().pin_memory()
     Xe = torch.zeros_like(X)
     idx_host = [torch.from_numpy(np.ascontiguousarray(b, dtype=np.int32)) for b in batches]
@@ -405,6 +514,8 @@ def run_gpu(args, rank, world, w):
         nonlocal h2d, d2h
         done = []
         for j, k in enumerate(ks):
+            if do_flush:
+                flush.fill_(float(k))
             fl = flags | (binding.SMDD_REUSE_XHAT if k > 0 else 0)
             binding.smdd_step_host(plan.handle, Xe, U_host, idx_host[k], alpha, fl, loss_host[k:k + 1], stream)
             e = torch.cuda.Event()
@@ -433,50 +544,26 @@ def run_gpu(args, rank, world, w):
     if rank != 0:
         return None
 
-    peaks, peak_src = load_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    clocks = clk.summary()
-    # dominant kernel: largest share of the device time of the timed steps
-    st = {k: v for k, v in stage.items() if v[1] > 0 and k in ("rfft", "cgemm_fwd", "residual", "cgemm_adj", "update")}
-    dom = max(st, key=lambda k: st[k][0])
-    dom_ms = st[dom][0] / st[dom][1]
-    kw = kernel_work(dom, nt, nr, nv, nb)
-    if dom in ("cgemm_fwd", "cgemm_adj") and args.precision == "fp32":
-        peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
-        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dom, args.workload),
-                "kernel": dom, "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                                             f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
-    else:
-        peak = float(peaks["hbm_gbs"])
-        ach = kw["bytes"] / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dom, args.workload),
-                "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    roof["algorithmic_per_launch"] = kw["bytes"] if roof["bound"] == "hbm" else kw["flops"]
-    roof["launch_ms"] = round(dom_ms, 5)
-    stage_share = {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": v[1],
-                       "share": round(v[0] / sum(x[0] for x in st.values()), 4)} for k, v in st.items()}
-
-    # step-level roofline: max(compulsory bytes / HBM, flops / FP32 ALU peak)
-    # FP32 peak: measured FMA throughput (probe launched after the timed region), lane count x clock beside it
-    fp32_derived = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = binding.alu_peak_tflops(0)
-    fp64_peak = binding.alu_peak_tflops(1)
-    t_roof = max(step_bytes_compulsory(nt, nr, nv, nb, recip) / (peaks["hbm_gbs"] * 1e9),
-                 step_flops(nt, nr, nv, nb) / (fp32_peak * 1e12))
+    peaks, fp64_peak = measured_peaks(dev)
+    kern = stage_roofs(peaks, stage, (nt, nr, nv, nb), tc)
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    roof = dict(kern[dom])
+    roof["traffic"] = ncu_traffic(dom, args.workload)
+    t_roof = peaks.step_roof_s(nt, nr, nv, nb, recip, tc)
     ms_per_step = t_dev / args.steps * 1e3
+    nfft_impl, _ = binding.mdc_plan_info(plan.handle)
 
     out = {
         "metric": METRIC, "value": round(flops_all / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
+        "dtype": "f32" if not tc else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
         "data": "synthetic (seeded Ricker/hyperbola generator; U_obs = GPU forward of the true model + 5% noise)",
         "config": {"workload": args.workload, "nt": nt, "nr": nr, "nv": nv, "ns": ns, "nb": nb,
-                   "nfft": nfft_for(nt), "reciprocity": recip, "precision": args.precision, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
-                   "l2": ("flushed before every timed step (256 MiB write, outside the step events)" if do_flush else
+                   "nfft_algorithmic": nfft_for(nt), "nfft_library": nfft_impl, "reciprocity": recip,
+                   "precision": args.precision, "solver": "SGD, alpha = 0.5 * 2/sigma^2_max",
+                   "l2": ("flushed before every step (256 MiB write, outside the step events; also in the e2e loop)"
+                          if do_flush else
                           f"inputs larger than L2: no flush, back-to-back steps (per-step traffic "
                           f"{step_traffic / 2**20:.0f} MiB against {l2_bytes / 2**20:.0f} MiB of L2)"),
                    "per_rank": "independent problem replica, seed = rank (no data-path collective)",
@@ -485,13 +572,16 @@ def run_gpu(args, rank, world, w):
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches) * world,
         "roofline": roof,
-        "stage_share": stage_share,
+        "kernels": kern,
         "step_roofline": {"t_roof_us": round(t_roof * 1e6, 2), "t_step_us": round(ms_per_step * 1e3, 2),
                           "frac": round(t_roof / (ms_per_step * 1e-3), 4),
-                          "definition": "max(compulsory bytes / measured HBM GB/s, algorithmic flops / measured FP32 FMA peak)",
-                          "fp32_tflops_measured": round(fp32_peak, 2), "fp32_tflops_derived": round(fp32_derived, 2),
+                          "definition": ("max(compulsory bytes / HBM, F_gemm / P_gemm + F_fft / P_FP32); P_gemm = "
+                                         + ("sustained BF16 tensor rate" if tc else "measured FP32 FMA rate")),
+                          "fp32_tflops_measured": round(peaks.fp32 / 1e12, 2),
+                          "fp32_tflops_derived": round(peaks.fp32_derived, 2),
+                          "bf16_tflops_sustained": round(peaks.bf16 / 1e12, 1),
                           "fp64_tflops_measured": round(fp64_peak, 3)},
-        "clocks": clocks,
+        "clocks": clk.summary(),
         "steps_per_s": round(args.steps / t_dev, 2),
         "wall_s_timed_region": round(wall, 4),
         "loss_first_last": [float(losses[0]), float(losses[-1])],
@@ -528,7 +618,7 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
     batches = synth.epoch_batches(ns, nb, 2 * n_ep, seed=100 + rank)
     idx_dev = [[torch.from_numpy(b).to(dev) for b in ep] for ep in batches]
     xt_norm = X_true.double().norm().item()
-    res = {}
+    res, x_at = {}, {}
     for name, prec in (("fp32", binding.MDC_PREC_FP32), ("bf16x3", binding.MDC_PREC_BF16X3)):
         plan = binding.MDCPlan(D, nv, nb_max=nb, precision=prec)
         flags = binding.SMDD_RECIPROCITY if recip else 0
@@ -549,6 +639,8 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
             t += e0.elapsed_time(e1) / 1e3
             steps += len(idx_dev[ep])
             errs.append((X.double() - X_true.double()).norm().item() / xt_norm)
+            if ep + 1 == n_ep:
+                x_at[name] = X.clone()
             if target is not None and ep + 1 >= n_ep and errs[-1] <= target * (1 + 1e-3):
                 break
         if plan.sync_status() != binding.MDC_OK:
@@ -558,9 +650,39 @@ def precision_comparison(args, dev, D, U_obs, X_true, w, rank):
         plan.close()
     res["bf16x3_vs_fp32_steps_per_s"] = round(res["bf16x3"]["steps_per_s"] / res["fp32"]["steps_per_s"], 3)
     res["bf16x3_vs_fp32_time_to_error"] = round(res["fp32"]["device_s"] / res["bf16x3"]["device_s"], 3)
+    a, b = x_at["bf16x3"].double(), x_at["fp32"].double()
+    res["x_rel_l2_bf16x3_vs_fp32_after_n_epochs"] = float((a - b).norm() / b.norm())
+    res["nb"] = nb
+    res["tolerance"] = ("FP64-oracle parity of these paths (the -m gpu tests, nt 1024 301 x 301 x 401 batch 32, "
+                        "sampled columns): FP32 <= 1e-5 and BF16x3 <= 1e-4 relative L2 on U and the gradient; "
+                        "X after 50 epochs <= 1e-4 (FP32) and 1e-3 (BF16x3)")
     res["definition"] = ("same batches from X = 0; model error = ||X - X_true|| / ||X_true||; BF16x3 runs until "
                          "its error is within 0.1% of the FP32 error after the FP32 epochs (the two differ by "
                          "rounding only); device time of the steps")
+    return res
+
+
+def fixed_error_run(args, dev, name, rank):
+    """precision_comparison on a single-problem workload built here (the batched line carries it for the
+    mixed-precision workloads: nt 1024, 301 x 301 x 401, batch 32 and 64)."""
+    import torch
+
+    from paper_2202_04486_gb300 import binding
+
+    w = workload_dims(name)
+    p = make_inputs(w, seed=rank)
+    D = torch.from_numpy(p.D.astype(np.float32)).to(dev)
+    X_true = torch.from_numpy(p.X_true.astype(np.float32)).to(dev)
+    gen = binding.MDCPlan(D, w["nv"], nb_max=w["nb"])
+    U_obs = torch.empty((w["ns"], w["nv"], w["nt"]), device=dev)
+    for s0 in range(0, w["ns"], w["nb"]):
+        ii = torch.arange(s0, min(w["ns"], s0 + w["nb"]), device=dev, dtype=torch.int32)
+        gen.forward(X_true, ii, out=U_obs[s0:s0 + ii.numel()])
+    gen.close()
+    res = precision_comparison(args, dev, D, U_obs, X_true, w, rank)
+    res["workload"] = name
+    del D, X_true, U_obs
+    torch.cuda.empty_cache()
     return res
 
 
@@ -661,6 +783,32 @@ def solver_comparison(args, dev, D, U_obs, X_true, w, rank):
 BATCH_WORKLOAD = "smdd_batch48_nb32"
 
 
+def oracle_member_sample(m, target_s, seed=0):
+    """Time the oracle's forward + adjoint of one SGD step of batch member m (nt, nr, nv, nb) on a sample of
+    virtual-source columns sized to about target_s, extrapolated linearly in the column count.  The
+    direct sums cost the same for any values, so the batch rows of D and the model columns are seeded
+    random traces (no full-size FP64 generation on the host).  Returns (GFLOP/s, s per step, columns)."""
+    import oracle
+
+    nt, nr, nv, nb = m["nt"], m["nr"], m["nv"], m["nb"]
+    rng_seed = 7000 + seed
+    Dr = synth.random_traces((nb, nr, nt), rng_seed)
+    idx = np.arange(nb, dtype=np.int32)
+
+    def run(k):
+        Xs = synth.random_traces((k, nr, nt), rng_seed + 1)
+        t0 = time.perf_counter()
+        U = oracle.mdc_forward(Dr, Xs, idx)
+        oracle.mdc_adjoint(Dr, U, idx)
+        return time.perf_counter() - t0
+
+    per_col = max(run(1), 1e-6)
+    k = int(min(nv, max(1, target_s / per_col)))
+    t = run(k) if k > 1 else per_col
+    t_step = t * nv / k
+    return step_flops(nt, nr, nv, nb) / t_step / 1e9, t_step, k
+
+
 def run_gpu_batch(args, rank, world):
     import torch
 
@@ -676,7 +824,8 @@ def run_gpu_batch(args, rank, world):
     binding.load_library()
     specs = synth.batch_members(args.batch_n, seed=1000 + 100000 * rank,
                                 largest=(1500, 1200, 1200, 1200) if args.batch_largest else None)
-    prec = binding.MDC_PREC_BF16X3 if args.precision == "bf16x3" else binding.MDC_PREC_FP32
+    tc = args.precision == "bf16x3"
+    prec = binding.MDC_PREC_BF16X3 if tc else binding.MDC_PREC_FP32
     n_perm = args.warmup + args.steps
     members, setup = [], []
     t_setup = time.perf_counter()
@@ -698,12 +847,14 @@ def run_gpu_batch(args, rank, world):
         members.append(dict(plan=plan, X=torch.zeros((nv, nr, nt), device=dev), U_obs=U_obs,
                             perm=torch.from_numpy(perm).to(dev), nb=nb, alpha=alpha, flags=flags,
                             loss=torch.zeros((n_perm, steps), device=dev, dtype=torch.float64)))
-        setup.append(dict(m, steps=steps, cfg=cfg, perm_host=torch.from_numpy(perm).pin_memory()))
+        setup.append(dict(m, steps=steps, cfg=cfg, perm_host=torch.from_numpy(perm).pin_memory(),
+                          nfft_library=binding.mdc_plan_info(plan.handle)[0]))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     batch = binding.MDCBatch(members, n_branches=args.branches)
-    epoch_flops = sum(step_flops(m["nt"], m["nr"], m["nv"], min(m["nb"], m["ns"] - s * m["nb"]))
-                      for m in setup for s in range(m["steps"]))
+    step_sizes = [(m["nt"], m["nr"], m["nv"], min(m["nb"], m["ns"] - s * m["nb"]), m["reciprocity"])
+                  for m in setup for s in range(m["steps"])]
+    epoch_flops = sum(step_flops(nt, nr, nv, nb) for nt, nr, nv, nb, _ in step_sizes)
     stream = torch.cuda.current_stream()
 
     batch.run(0, args.warmup)
@@ -734,7 +885,7 @@ def run_gpu_batch(args, rank, world):
     loss_last = [float(m["loss"][args.warmup + args.steps - 1, -1]) for m in members]
 
     # e2e: every epoch's permutations go host -> device (pinned) before the replay and every member's
-    # step losses come back device -> host after it
+    # step losses come back device -> host after it (inputs larger than L2 in both loops: no flush)
     loss_host = [torch.empty_like(m["loss"][0], device="cpu").pin_memory() for m in members]
     h2d = d2h = 0
     torch.cuda.synchronize()
@@ -751,7 +902,7 @@ def run_gpu_batch(args, rank, world):
         stream.synchronize()
     t_e2e = time.perf_counter() - e0
 
-    # dominant kernel of the largest member, from a few profiled steps outside the graph
+    # per-kernel figures of the largest member, from a few profiled steps outside the graph
     big = max(range(len(setup)), key=lambda k: step_flops(setup[k]["nt"], setup[k]["nr"], setup[k]["nv"], setup[k]["nb"]))
     mb, sb = members[big], setup[big]
     plan = mb["plan"]
@@ -763,78 +914,121 @@ def run_gpu_batch(args, rank, world):
                           mb["flags"] | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if s else 0))
     stage = binding.mdc_plan_stage_times(plan.handle, reset=True)
     binding.mdc_plan_set_profiling(plan.handle, False)
-    peaks, peak_src = load_peaks()
-    st = {k: v for k, v in stage.items() if v[1] > 0 and k in ("cgemm_fwd", "residual", "cgemm_adj", "update")}
-    dom = max(st, key=lambda k: st[k][0] / st[k][1])
-    dom_ms = st[dom][0] / st[dom][1]
-    kw = kernel_work(dom, sb["nt"], sb["nr"], sb["nv"], sb["nb"])
-    if dom in ("cgemm_fwd", "cgemm_adj") and args.precision == "bf16x3":
-        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
-        pk = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
-        roof = {"bound": "tensor", "achieved": round(ach, 2), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
-                "traffic": None, "kernel": dom,
-                "peak_source": f"{peak_src} bf16 sustained (algorithmic complex flops, not the 9 split products)"}
-    elif dom in ("cgemm_fwd", "cgemm_adj"):
-        props = torch.cuda.get_device_properties(dev)
-        pk = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
-        ach = kw["flops"] / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 2), "peak": round(pk, 2), "unit": "TFLOP/s",
-                "frac": round(ach / pk, 4), "traffic": None, "kernel": dom, "peak_source": "derived FP32 SIMT peak"}
-    else:
-        pk = float(peaks["hbm_gbs"])
-        ach = kw["bytes"] / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
-                "traffic": None, "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    roof["launch_ms"] = round(dom_ms, 4)
-    roof["member"] = {k: sb[k] for k in ("nt", "nr", "nv", "ns", "nb")}
-    roof["stage_ms_per_launch"] = {k: round(v[0] / v[1], 4) for k, v in st.items()}
+    if plan.sync_status() != binding.MDC_OK:
+        raise RuntimeError("device status after the profiled steps")
 
     (t_dev, t_e2e, wall), flops_all = combine_ranks([t_dev, t_e2e, wall], epoch_flops * args.steps, dev)
     if rank != 0:
         return None
-    cfgs = {}
+    peaks, fp64_peak = measured_peaks(dev)
+    kern = stage_roofs(peaks, stage, (sb["nt"], sb["nr"], sb["nv"], sb["nb"]), tc)
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    roof = dict(kern[dom])
+    roof["traffic"] = ncu_traffic(dom, BATCH_WORKLOAD)
+    roof["member"] = {k: sb[k] for k in ("nt", "nr", "nv", "ns", "nb")}
+    t_roof_epoch = sum(peaks.step_roof_s(nt, nr, nv, nb, rc, tc) for nt, nr, nv, nb, rc in step_sizes)
+    ms_epoch = t_dev / args.steps * 1e3
+    cfgs, nffts = {}, {}
     for sp in setup:
         key = f"fft{sp['cfg']['fft_variant']}_fwd{sp['cfg']['gemm_fwd']}_adj{sp['cfg']['gemm_adj']}"
         cfgs[key] = cfgs.get(key, 0) + 1
+        nk = f"{sp['nt']}:{nfft_for(sp['nt'])}/{sp['nfft_library']}"
+        nffts[nk] = nffts.get(nk, 0) + 1
     out = {
         "metric": METRIC, "value": round(flops_all / t_dev / 1e9, 2), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_dev / args.steps * 1e3, 3),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_epoch, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
+        "dtype": "f32" if not tc else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
         "data": "synthetic (seeded Ricker/hyperbola generator per member, evaluated on the device; U_obs = GPU forward)",
         "config": {"workload": BATCH_WORKLOAD, "members": len(specs), "largest_member": bool(args.batch_largest),
                    "steps_per_epoch_all_members": sum(sp["steps"] for sp in setup), "nb": 32,
                    "precision": args.precision, "a_step_of_this_line": "one epoch of every member (one graph replay)",
                    "branches": batch.n_branches, "kernels_per_epoch": batch.kernels_per_epoch,
                    "autotuned": bool(args.autotune), "chosen_configs": cfgs,
+                   "members_by_nt_nfft_algorithmic_library": nffts,
                    "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1),
                    "per_rank": "independent member set, seeds offset by rank (no data-path collective)"},
         "e2e": {"value": round(flops_all / t_e2e / 1e9, 2), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": int(launches) * world,
         "roofline": roof,
+        "kernels_largest_member": kern,
+        "step_roofline": {"t_roof_ms_per_epoch": round(t_roof_epoch * 1e3, 3), "t_epoch_ms": round(ms_epoch, 3),
+                          "frac": round(t_roof_epoch / (ms_epoch * 1e-3), 4),
+                          "definition": ("sum over every step of every member of max(compulsory bytes / HBM, "
+                                         "F_gemm / P_gemm + F_fft / P_FP32); P_gemm = "
+                                         + ("sustained BF16 tensor rate" if tc else "measured FP32 FMA rate")),
+                          "fp32_tflops_measured": round(peaks.fp32 / 1e12, 2),
+                          "fp32_tflops_derived": round(peaks.fp32_derived, 2),
+                          "bf16_tflops_sustained": round(peaks.bf16 / 1e12, 1),
+                          "fp64_tflops_measured": round(fp64_peak, 3)},
         "clocks": clk.summary(),
         "epochs_per_s": round(args.steps / t_dev, 3),
         "wall_s_timed_region": round(wall, 3),
         "loss_first_last_sum": [sum(loss_first), sum(loss_last)],
     }
-    # oracle on the host cores: the smallest member, a column sample of one step
-    small = min(specs, key=lambda m: m["nt"] * m["nr"] * m["nv"])
-    w = dict(small)
-    p = synth.make_problem(w["nt"], w["nr"], w["nv"], w["ns"], dx=w["dx"], n_reflectors=w["n_reflectors"],
-                           n_multiples=w["n_multiples"], seed=w["seed"])
-    D64 = p.D.astype(np.float32).astype(np.float64)
-    Uo = np.zeros((w["ns"], w["nv"], w["nt"]))
-    bt = synth.epoch_batches(w["ns"], w["nb"], 1, seed=w["seed"])
-    val, t_step, sample, cores = time_oracle(w, D64, np.zeros((w["nv"], w["nr"], w["nt"])), Uo, bt, target_s=10.0)
-    out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                           "sample": f"member nt={w['nt']} nr={w['nr']} nv={w['nv']} ns={w['ns']}: " + sample}
+    # release the members before the mixed-precision comparison
+    batch.close()
+    for m in members:
+        m["plan"].close()
+    members.clear()
+    torch.cuda.empty_cache()
+    if args.fixed_error_epochs > 0:
+        out["fixed_error"] = {name.rsplit("_", 1)[-1]: fixed_error_run(args, dev, name, rank)
+                              for name in FIXED_ERROR_WORKLOADS}
+    # oracle on the host cores: one step of the largest member on a column sample
+    val, t_step, k = oracle_member_sample(sb, args.oracle_seconds)
+    import oracle
+    out["cpu_baseline"] = {"value": round(val, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                           "sample": (f"largest member (nt {sb['nt']}, {sb['nr']} x {sb['nv']}, batch {sb['nb']}): FP64 "
+                                      f"direct-sum forward + adjoint of one step on {k} of {sb['nv']} virtual-source "
+                                      f"columns, extrapolated linearly in the column count"),
+                           "s_per_step_extrapolated": round(t_step, 2)}
     return out
 
 
 # ------------------------------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ------------------------------------------------------------------------------------------------
+def run_reference_batch(args, rank, world):
+    """The oracle on the batched workload: each of the W + K steps of this arm times one SGD step of one
+    member (members in turn, largest first) on a column sample of about 150 / (W + K) seconds,
+    extrapolated to the member's full step; the K timed samples give the epoch-weighted rate
+    sum(steps_m F_m) / sum(steps_m t_m) over the members they cover."""
+    if rank != 0:
+        return None
+    import oracle
+    specs = synth.batch_members(args.batch_n, seed=1000, largest=(1500, 1200, 1200, 1200) if args.batch_largest else None)
+    for m in specs:
+        m["steps"] = -(-m["ns"] // m["nb"])
+    order = sorted(specs, key=lambda m: -step_flops(m["nt"], m["nr"], m["nv"], m["nb"]))
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    f_tot = t_tot = 0.0
+    used = []
+    for k in range(args.warmup + args.steps):
+        # warm-up samples on the smallest members, timed samples from the largest member on
+        m = order[(k - args.warmup) % len(order)] if k >= args.warmup else order[-1 - k % len(order)]
+        val, t_step, cols = oracle_member_sample(m, budget, seed=k)
+        if k >= args.warmup:
+            f_tot += m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"])
+            t_tot += m["steps"] * t_step
+            used.append(f"{m['nt']}/{m['nr']}x{m['nv']}:{cols}")
+    val = f_tot / t_tot / 1e9
+    epoch_flops = sum(m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"]) for m in specs)
+    sample = ("each step: FP64 direct-sum forward + adjoint of one SGD step of one member (largest first, in "
+              "turn) on a column sample, extrapolated in the column count; epoch-weighted over the members "
+              "timed (nt/nr x nv:columns): " + ", ".join(used) + "; ms_per_step = the epoch of all members at "
+              "that rate")
+    return {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(epoch_flops / (val * 1e9) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "seeded random traces of each member's shape (the direct sums cost the same for any values)",
+            "config": {"workload": BATCH_WORKLOAD, "members": len(specs), "nb": 32},
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, rank, world, w):
     if rank != 0:
         return None
@@ -883,7 +1077,7 @@ def run_reference(args, rank, world, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
@@ -897,42 +1091,40 @@ def main():
     ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
     ap.add_argument("--solver-epochs", type=int, default=0,
                     help="also compare SGD, N-SGD and full-gradient LSQR over this many epochs (model error per epoch)")
-    ap.add_argument("--l2", default="flush", choices=["auto", "flush", "none"],
-                    help="L2 between timed steps: flush (default), none, or auto (flush unless a step moves > 4x L2; "
-                         "measured within 0.5%% of flush on the default workload)")
-    ap.add_argument("--fixed-error-epochs", type=int, default=0,
-                    help="also compare FP32 and BF16x3 products at the same final-model error after this many epochs")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"],
-                    help="arithmetic of the per-frequency products (the FFTs are FP32 in both)")
+    ap.add_argument("--l2", default="auto", choices=["auto", "flush", "none"],
+                    help="L2 between timed steps (single problems): auto (default: flush unless a step moves > 4x L2), "
+                         "flush, or none; the end-to-end loop follows the same policy")
+    ap.add_argument("--fixed-error-epochs", type=int, default=None,
+                    help="compare FP32 and BF16x3 products at the same final-model error after this many epochs "
+                         f"(default: 50 on {BATCH_WORKLOAD}, where it runs the nt 1024 301 x 301 x 401 workload at "
+                         "batch 32 and 64; 0 elsewhere)")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0, help="CPU time of the oracle sample for cpu_baseline")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16x3"],
+                    help=f"arithmetic of the per-frequency products (the FFTs are FP32 in both); default "
+                         f"{DEFAULT_PRECISION} on {BATCH_WORKLOAD}, fp32 elsewhere")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    batch_mode = args.workload == BATCH_WORKLOAD
+    if args.precision is None:
+        args.precision = DEFAULT_PRECISION if batch_mode else "fp32"
+    if args.fixed_error_epochs is None:
+        args.fixed_error_epochs = 50 if batch_mode else 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if args.workload == BATCH_WORKLOAD:
-        if args.impl == "reference":
-            ap.error(f"--impl reference times single problems; {BATCH_WORKLOAD} has no reference arm")
-        if world > 1:
-            import torch
-            torch.distributed.init_process_group("nccl")
-        out = run_gpu_batch(args, rank, world)
-        if world > 1:
-            import torch
-            torch.distributed.destroy_process_group()
+    if args.impl == "reference":
+        out = run_reference_batch(args, rank, world) if batch_mode else run_reference(args, rank, world,
+                                                                                     workload_dims(args.workload))
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    w = workload_dims(args.workload)
-    if args.impl == "reference":
-        out = run_reference(args, rank, world, w)
-    else:
-        if world > 1:
-            import torch
-            torch.distributed.init_process_group("nccl")
-        out = run_gpu(args, rank, world, w)
-        if world > 1:
-            import torch
-            torch.distributed.destroy_process_group()
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu_batch(args, rank, world) if batch_mode else run_gpu(args, rank, world, workload_dims(args.workload))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -52,7 +52,7 @@ typedef enum {
     MDC_ERR_OOM = 4,           /* device allocation failed in mdc_plan_create */
     MDC_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
     MDC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (tensor-core products) */
-    MDC_ERR_UNSUPPORTED = 7    /* size outside the supported range (nt > 4096, nfft not a power of two) */
+    MDC_ERR_UNSUPPORTED = 7    /* size outside the supported range (nt > 4096, an unsupported nfft) */
 } mdc_status;
 
 /* Arithmetic of the per-frequency products (the FFTs are FP32 in both):
@@ -68,8 +68,9 @@ typedef enum { MDC_PREC_FP32 = 0, MDC_PREC_BF16X3 = 1 } mdc_precision;
  *   nt      : time samples per trace, 1 <= nt <= 4096.
  *   nr, nv, ns : receivers, virtual sources, sources (>= 1).
  *   nb_max  : largest batch size later passed to any call (1 <= nb_max <= 1024; 0 means ns).
- *   nfft    : FFT length; 0 picks the smallest power of two >= max(2*nt-1, 64).  A non-zero value
- *             must be a power of two >= 2*nt-1 and <= 8192.
+ *   nfft    : FFT length; 0 picks the shortest supported length >= max(2*nt-1, 64).  Supported: the
+ *             powers of two 64 .. 8192 and 3072 = 3 * 2^10 (chosen for 1025 <= nt <= 1536, where the
+ *             power of two would be 4096).  A non-zero value must be supported and >= 2*nt-1.
  *   scale   : multiplies the operator (the discretisation of the receiver integral in Eq. 1; 1 is a
  *             plain sum over receivers).
  *   D       : device pointer, [ns][nr][nt] float32, read during this call only.
@@ -144,7 +145,7 @@ int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx,
 int smdd_step_host(mdc_plan_t plan, float *X, const float *U_obs_host, const int32_t *idx_host, int nb,
                    const smdd_params *params, double *loss_host, void *stream);
 
-/* smdd_step_ex: the same step with the N-SGD solver and the causality preconditioner.
+/* smdd_step_ex: the same step with the N-SGD solver, the Adam update and the causality preconditioner.
  * N-SGD is SGD with Nesterov momentum in the form of Sutskever et al. (2013) -- the solver the paper
  * reports as converging fastest -- written on the look-ahead point: with g the preconditioned batch
  * gradient evaluated at X,
@@ -155,16 +156,28 @@ int smdd_step_host(mdc_plan_t plan, float *X, const float *U_obs_host, const int
  * reciprocity first; with SMDD_RECIPROCITY the mute table must be symmetric (mute[v][r] == mute[r][v]),
  * so that the two projections commute and X stays in the range of C. */
 #define SMDD_NESTEROV       16  /* smdd_step_ex only: momentum with velocity state V */
+/* Adam (Kingma & Ba 2015, Algorithm 1; the paper itself uses SGD and N-SGD) on the preconditioned batch
+ * gradient g, element-wise, with moment arrays m = V and v = S and step count t >= 1:
+ *   m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+ *   X <- X - alpha * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * The bias corrections are formed in double precision on the host and rounded to float once; the
+ * element-wise arithmetic is float32.  Muted samples see g = 0, so a model and moments that start zero
+ * there stay zero there; with reciprocity a symmetric start stays symmetric. */
+#define SMDD_ADAM           32  /* smdd_step_ex only: Adam with moments V (first) and S (second) */
 
 typedef struct {
     float alpha;            /* step size */
-    int flags;              /* SMDD_* bits, SMDD_NESTEROV included */
+    int flags;              /* SMDD_* bits, SMDD_NESTEROV or SMDD_ADAM included */
     float mu;               /* momentum, 0 <= mu < 1 (SMDD_NESTEROV) */
-    int reserved0;          /* zero */
-    float *V;               /* SMDD_NESTEROV: velocity [nv][nr][nt] device float32, updated in place (start
-                               from zeros); NULL without SMDD_NESTEROV; never the same array as X */
+    int t;                  /* SMDD_ADAM: step count, 1 for the first step (bias corrections); else 0 */
+    float *V;               /* SMDD_NESTEROV: velocity; SMDD_ADAM: first moment m.  [nv][nr][nt] device
+                               float32, updated in place (start from zeros); NULL otherwise; never X */
     const int32_t *mute;    /* causality mute: device int32[nv][nr], first kept sample per model trace; or NULL */
-    int reserved[4];        /* zero */
+    float *S;               /* SMDD_ADAM: second moment v, [nv][nr][nt] device float32 (start from zeros),
+                               distinct from X and V; NULL otherwise */
+    float beta1, beta2;     /* SMDD_ADAM: moment decay rates in [0, 1) (Kingma & Ba: 0.9, 0.999) */
+    float eps;              /* SMDD_ADAM: > 0, added to the root of the corrected second moment */
+    int reserved;           /* zero */
 } smdd_step_ex_params;
 
 int smdd_step_ex(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx, int nb,
@@ -193,11 +206,14 @@ int smdd_lsqr(mdc_plan_t plan, float *X, const float *U_obs, int n_iter, int fla
  * nfft the default length.  Every intermediate lives in one static 64 MiB device array that the library
  * holds on each device where this function has been used, until the process exits.
  *   D [ns][nr][nt], X [nv][nr][nt], idx int32[nb], U [nb][nv][nt]: device pointers owned by the caller.
- *   dev_status: device int (or NULL) set to 1 if an index lies outside [0, ns); the caller zeroes it.
+ *   dev_status: device int, required (MDC_ERR_INVALID_ARG when NULL): set to 1 if an index lies outside
+ *               [0, ns), whose rows of U are then zero; the caller zeroes it and reads it after the stream
+ *               has passed the call.
  *   stream: as elsewhere.
  * Returns MDC_ERR_UNSUPPORTED, launching nothing, when the intermediates of the problem need more than
  * the 64 MiB: 8 * (nfft/2+1) * (ns*ldr + nv*ldr + nv*ldb) bytes plus the twiddle tables, with ldr and ldb
- * nr and nb rounded up to even.
+ * nr and nb rounded up to even.  Shapes are not checked here (there is no plan): the caller must pass
+ * arrays of exactly the sizes above.
  * The first call on a device looks up the array's device address (once per device) and must therefore
  * not be the first call made during a stream capture.  All calls share the array: two calls that can
  * overlap on the GPU (other streams, other host threads) race with each other and must be serialised
@@ -299,6 +315,18 @@ int mdc_batch_run(mdc_batch_t batch, long long first_epoch, int n_epochs, void *
 int mdc_batch_info(mdc_batch_t batch, long long *kernels_per_epoch, int *n_branches);
 /* Release the graph and the batch's buffers (synchronises the device first; the plans stay). */
 int mdc_batch_destroy(mdc_batch_t batch);
+
+/* Failure-path check of the bounded waits (the paper has no counterpart; Eq. 2 and 6 are what the
+ * checked kernels compute).  Every mbarrier wait of the split-BF16 product kernels is bounded (about a
+ * second of SM clock); a CTA whose wait gives up records MDC_ERR_TIMEOUT in the plan's status word,
+ * writes no products, lets products still in flight finish (one more bounded wait), frees its tensor
+ * memory and returns, so the context stays usable.  With cycles > 0 every CTA of the tile kernels
+ * (MDC_GEMM_TC; the streamed forward kernel ignores it) first waits on an mbarrier that nothing arrives
+ * on, for `cycles` SM clock cycles, before any copy or product is issued, and then takes that path: the
+ * call's products are not written (the spectral workspaces keep their previous contents) and
+ * mdc_plan_sync_status returns MDC_ERR_TIMEOUT.  0 (the default) turns it off.
+ * MDC_ERR_INVALID_ARG for cycles < 0 or > 1e8.  Captured graphs keep the value they were captured with. */
+int mdc_plan_set_wait_probe(mdc_plan_t plan, long long cycles);
 
 /* Wait for all work of this plan's device, then return and clear the device-side status word
  * (MDC_OK, MDC_ERR_INDEX_RANGE, or MDC_ERR_TIMEOUT when a bounded wait of a tensor-core kernel gave up). */

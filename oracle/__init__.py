@@ -21,7 +21,7 @@ N-SGD: the equivalence of the look-ahead form with Sutskever's form, mu = 0 givi
 to the minimum-norm least-squares solution; the causality mute against an explicit loop; LSQR against
 scipy's implementation and the least-squares solution.
 
-Readings of the paper taken here (each is also listed in the design notes):
+Readings of the paper taken here, where its text is silent or ambiguous:
   * scale: the receiver integral of Eq. 1 is a plain sum over receivers times `scale` (default 1).
   * gradient: g_B = P_B^H (P_B X - U_B), summed (not averaged) over the batch; the update is
     X <- X - alpha * C(g_B) (Eq. 6 with its leading minus folded into the residual).
@@ -264,6 +264,26 @@ def nsgd_step(D, X, V, U_obs, idx, alpha: float, mu: float, *, recip: bool = Fal
     return X_new, V_new, l
 
 
+def adam_step(D, X, M, V, U_obs, idx, alpha: float, t: int, *, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, recip: bool = False, mute=None, scale: float = 1.0, fft: bool = False):
+    """One step of Adam (Kingma & Ba 2015, Algorithm 1) on the preconditioned mini-batch gradient
+    C^T g_B of Eq. 6 (the paper's solvers are SGD and N-SGD; Adam is the other update asked of the fused
+    kernel).  With t >= 1 the step count:
+        m <- beta1 m + (1 - beta1) g,      v <- beta2 v + (1 - beta2) g^2          (biased moments)
+        m_hat = m / (1 - beta1^t),         v_hat = v / (1 - beta2^t)               (bias corrections)
+        x <- x - alpha m_hat / (sqrt(v_hat) + eps)                                  (element-wise)
+    Returns (X_new, M_new, V_new, loss)."""
+    assert t >= 1
+    g, l, _ = gradient(D, X, U_obs, idx, scale, fft)
+    g = precondition(g, recip=recip, mute=mute)
+    M_new = beta1 * _f64(M) + (1.0 - beta1) * g
+    V_new = beta2 * _f64(V) + (1.0 - beta2) * g * g
+    m_hat = M_new / (1.0 - beta1 ** t)
+    v_hat = V_new / (1.0 - beta2 ** t)
+    X_new = _f64(X) - alpha * m_hat / (np.sqrt(v_hat) + eps)
+    return X_new, M_new, V_new, l
+
+
 def lsqr(apply_A, apply_At, b, x0, n_iter: int):
     """LSQR (Paige & Saunders 1982, the bidiagonalisation algorithm of their Section 4) for
     min ||A x - b||, the full-gradient MDD solver the paper compares against.  apply_A / apply_At are
@@ -331,11 +351,6 @@ def sigma2_max(D, nfft: int | None = None, scale: float = 1.0) -> float:
     Dh = np.fft.rfft(D, n=nfft, axis=-1)                            # (ns, nr, nf)
     s = np.linalg.svd(np.moveaxis(Dh, -1, 0), compute_uv=False)     # (nf, min(ns,nr))
     return float(scale * scale * np.max(s[:, 0] ** 2))
-
-
-def landweber_alpha(sigma2: float, kappa: float) -> float:
-    """Step size kappa * 2 / sigma^2 (Appendix B; kappa < 1 is inside the Landweber bound)."""
-    return kappa * 2.0 / sigma2
 
 
 def landweber(A, y, alpha: float, n_iter: int, x0=None) -> np.ndarray:

@@ -30,6 +30,7 @@ SMDD_KEEP_XHAT = 2
 SMDD_REUSE_XHAT = 4
 SMDD_UOBS_GATHERED = 8
 SMDD_NESTEROV = 16
+SMDD_ADAM = 32
 
 MDC_NUM_STAGES = 7
 
@@ -49,7 +50,7 @@ EXPORTED = (
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
     "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex", "smdd_lsqr", "mdc_plan_set_band",
     "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy", "mdc_alu_probe",
-    "smdd_step_host",
+    "smdd_step_host", "mdc_plan_set_wait_probe",
 )
 
 
@@ -64,8 +65,9 @@ class smdd_params(ctypes.Structure):
 
 
 class smdd_step_ex_params(ctypes.Structure):
-    _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("mu", ctypes.c_float), ("reserved0", ctypes.c_int),
-                ("V", ctypes.c_void_p), ("mute", ctypes.c_void_p), ("reserved", ctypes.c_int * 4)]
+    _fields_ = [("alpha", ctypes.c_float), ("flags", ctypes.c_int), ("mu", ctypes.c_float), ("t", ctypes.c_int),
+                ("V", ctypes.c_void_p), ("mute", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("reserved", ctypes.c_int)]
 
 
 class mdc_config(ctypes.Structure):
@@ -124,6 +126,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_plan_launch_count.argtypes = [vp]
     lib.mdc_alu_probe.argtypes = [i, i, i, vp, ctypes.POINTER(d), vp]
     lib.smdd_step_host.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(smdd_params), vp, vp]
+    lib.mdc_plan_set_wait_probe.argtypes = [vp, ctypes.c_longlong]
     lib.mdc_plan_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
         if name not in ("mdc_status_string", "mdc_stage_name", "mdc_plan_launch_count"):
@@ -159,6 +162,11 @@ def _dev(t: torch.Tensor, name: str, dtype, shape=None) -> ctypes.c_void_p:
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _shape(t: torch.Tensor, name: str, shape) -> None:
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
 def _require_cuda():
@@ -245,11 +253,16 @@ def smdd_step_host(plan: int, X: torch.Tensor, U_obs_host: torch.Tensor, idx_hos
 
 def smdd_step_ex(plan: int, X: torch.Tensor, U_obs: torch.Tensor, idx: torch.Tensor, alpha: float, flags: int = 0,
                  V: torch.Tensor | None = None, mu: float = 0.0, mute: torch.Tensor | None = None,
-                 loss: torch.Tensor | None = None, stream=None) -> None:
-    """N-SGD (flags with SMDD_NESTEROV and a velocity V) and/or the causality mute (int32 [nv][nr])."""
-    p = smdd_step_ex_params(float(alpha), int(flags), float(mu), 0,
+                 loss: torch.Tensor | None = None, stream=None, S: torch.Tensor | None = None, t: int = 0,
+                 beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    """N-SGD (flags with SMDD_NESTEROV and a velocity V), Adam (SMDD_ADAM, moments V and S, step count t
+    from 1) and/or the causality mute (int32 [nv][nr])."""
+    adam = bool(flags & SMDD_ADAM)
+    p = smdd_step_ex_params(float(alpha), int(flags), float(mu), int(t) if adam else 0,
                             None if V is None else _dev(V, "V", torch.float32, tuple(X.shape)).value,
-                            None if mute is None else _dev(mute, "mute", torch.int32, (X.shape[0], X.shape[1])).value)
+                            None if mute is None else _dev(mute, "mute", torch.int32, (X.shape[0], X.shape[1])).value,
+                            None if S is None else _dev(S, "S", torch.float32, tuple(X.shape)).value,
+                            float(beta1) if adam else 0.0, float(beta2) if adam else 0.0, float(eps) if adam else 0.0, 0)
     lp = ctypes.c_void_p(0) if loss is None else _dev(loss, "loss", torch.float64)
     _check(load_library().smdd_step_ex(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
                                        _dev(U_obs, "U_obs", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
@@ -264,6 +277,11 @@ def smdd_lsqr(plan: int, X: torch.Tensor, U_obs: torch.Tensor, n_iter: int, flag
     _check(load_library().smdd_lsqr(ctypes.c_void_p(plan), _dev(X, "X", torch.float32),
                                     _dev(U_obs, "U_obs", torch.float32), int(n_iter), int(flags), mp, npp,
                                     _stream_ptr(stream)), "smdd_lsqr")
+
+
+def mdc_plan_set_wait_probe(plan: int, cycles: int) -> None:
+    """Failure-path check of the tensor-core kernels' bounded waits (0 = off); see include/smdd.h."""
+    _check(load_library().mdc_plan_set_wait_probe(ctypes.c_void_p(plan), int(cycles)), "mdc_plan_set_wait_probe")
 
 
 def mdc_plan_sync_status(plan: int) -> int:
@@ -320,17 +338,36 @@ def alu_peak_tflops(kind: int = 0, iters: int | None = None, repeats: int = 5) -
     return flops / times[len(times) // 2] / 1e12
 
 
+def _static_shapes(D, X, idx, U, dev_status) -> tuple[int, int, int, int, int]:
+    """Shapes of an mdc_forward_static call, checked before anything reaches the library: the entry
+    point has no plan to check them against, and a wrong size would make its kernels read or write
+    outside the caller's arrays.  Returns (nt, nr, nv, ns, nb)."""
+    if D.dim() != 3:
+        raise ValueError(f"D must be [ns][nr][nt], got shape {tuple(D.shape)}")
+    ns, nr, nt = D.shape
+    if idx.dim() != 1 or idx.numel() < 1:
+        raise ValueError(f"idx must be a non-empty 1-D tensor, got shape {tuple(idx.shape)}")
+    if X.dim() != 3 or tuple(X.shape[1:]) != (nr, nt):
+        raise ValueError(f"X has shape {tuple(X.shape)}, expected (nv, {nr}, {nt})")
+    nv, nb = X.shape[0], idx.numel()
+    if tuple(U.shape) != (nb, nv, nt):
+        raise ValueError(f"U has shape {tuple(U.shape)}, expected {(nb, nv, nt)}")
+    if dev_status is None or dev_status.numel() != 1:
+        raise ValueError("dev_status must be a one-element int32 tensor (index errors are reported there)")
+    return nt, nr, nv, ns, nb
+
+
 def mdc_forward_static(D: torch.Tensor, X: torch.Tensor, idx: torch.Tensor, U: torch.Tensor, scale: float = 1.0,
                        dev_status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Forward MDC through the allocation-free entry point (no plan; intermediates in the library's
-    static device scratch).  Shapes as for mdc_forward; D is [ns][nr][nt]."""
+    static device scratch).  D [ns][nr][nt], X [nv][nr][nt], idx int32 [nb], U [nb][nv][nt]; dev_status
+    a device int32 scalar the caller zeroes, set to 1 when an index lies outside [0, ns)."""
+    nt, nr, nv, ns, nb = _static_shapes(D, X, idx, U, dev_status)
     _require_cuda()
-    ns, nr, nt = D.shape
-    nv = X.shape[0]
-    st = ctypes.c_void_p(0) if dev_status is None else _dev(dev_status, "dev_status", torch.int32)
     _check(load_library().mdc_forward_static(nt, nr, nv, ns, float(scale), _dev(D, "D", torch.float32),
-                                             _dev(X, "X", torch.float32), _dev(idx, "idx", torch.int32), idx.numel(),
-                                             _dev(U, "U", torch.float32), st, _stream_ptr(stream)), "mdc_forward_static")
+                                             _dev(X, "X", torch.float32), _dev(idx, "idx", torch.int32), nb,
+                                             _dev(U, "U", torch.float32), _dev(dev_status, "dev_status", torch.int32),
+                                             _stream_ptr(stream)), "mdc_forward_static")
     return U
 
 
@@ -448,22 +485,44 @@ class MDCPlan:
     def sigma2_max(self, n_iter: int = 60) -> float:
         return mdc_plan_sigma2_max(self.handle, n_iter)
 
+    def _model(self, X, name="X"):
+        _shape(X, name, (self.nv, self.nr, self.nt))
+
+    def _data(self, U, nb, name):
+        _shape(U, name, (nb, self.nv, self.nt))
+
     def forward(self, X: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._model(X)
         if out is None:
             out = torch.empty((idx.numel(), self.nv, self.nt), device=X.device, dtype=torch.float32)
+        self._data(out, idx.numel(), "out")
         return mdc_forward(self.handle, X, idx, out)
 
     def adjoint(self, R: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._data(R, idx.numel(), "R")
         if out is None:
             out = torch.empty((self.nv, self.nr, self.nt), device=R.device, dtype=torch.float32)
+        self._model(out, "out")
         return mdc_adjoint(self.handle, R, idx, out)
 
+    def _step_shapes(self, X, U_obs, idx, flags):
+        self._model(X)
+        self._data(U_obs, idx.numel() if flags & SMDD_UOBS_GATHERED else self.ns, "U_obs")
+
     def step(self, X, U_obs, idx, alpha, flags=0, loss=None):
+        self._step_shapes(X, U_obs, idx, flags)
         smdd_step(self.handle, X, U_obs, idx, alpha, flags, loss)
 
     def step_nsgd(self, X, V, U_obs, idx, alpha, mu=0.9, flags=0, mute=None, loss=None):
         """N-SGD step (Nesterov momentum, velocity V) with the optional causality mute."""
+        self._step_shapes(X, U_obs, idx, flags)
         smdd_step_ex(self.handle, X, U_obs, idx, alpha, flags | SMDD_NESTEROV, V=V, mu=mu, mute=mute, loss=loss)
+
+    def step_adam(self, X, M, V, U_obs, idx, alpha, t, beta1=0.9, beta2=0.999, eps=1e-8, flags=0, mute=None, loss=None):
+        """Adam step t (from 1) with first / second moments M, V and the optional causality mute."""
+        self._step_shapes(X, U_obs, idx, flags)
+        smdd_step_ex(self.handle, X, U_obs, idx, alpha, flags | SMDD_ADAM, V=M, mute=mute, loss=loss, S=V, t=t,
+                     beta1=beta1, beta2=beta2, eps=eps)
 
     def lsqr(self, X, U_obs, n_iter, flags=0, mute=None, norms=None):
         """Full-gradient LSQR over every source (the plan needs nb_max >= ns); X: start in, solution out."""

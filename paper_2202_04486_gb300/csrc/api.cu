@@ -35,6 +35,19 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
 
+namespace smdd {
+
+bool nfft_supported(int nfft) { return (is_pow2(nfft) && nfft >= 64 && nfft <= 8192) || nfft == 3072; }
+
+int default_nfft(int nt) {
+    // the shortest supported length >= max(2 nt - 1, 64): powers of two and 3072 = 3 * 2^10
+    int n = 64;
+    while (n < 2 * nt - 1) n *= 2;
+    return (n == 4096 && 2 * nt - 1 <= 3072) ? 3072 : n;
+}
+
+}  // namespace smdd
+
 struct mdc_plan_s {
     int device = 0;
     int nt = 0, nr = 0, nv = 0, ns = 0, nbmax = 0, nfft = 0, M = 0, nf = 0;
@@ -65,6 +78,7 @@ struct mdc_plan_s {
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
     int nf_active = 0;           // band limit of the products (0: every bin)
+    long long wait_probe = 0;    // failure-path check of the tensor-core kernels (cycles; 0 = off)
     // host-input steps (smdd_step_host): two device staging slots, filled on a copy stream
     struct HostStage {
         float *U[2] = {nullptr, nullptr};              // [nbmax][nv][nt] batch rows
@@ -195,6 +209,7 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.outscale = 1.f;
     g.status = p->status;
     g.nf_active = p->nf_active;
+    g.wait_probe = p->wait_probe;
     if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
     if (p->gemm_fwd == MDC_GEMM_TC_STREAM && p->xh_map_ok)
@@ -218,6 +233,7 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.outscale = recip ? 0.5f : 1.f;
     g.status = p->status;
     g.nf_active = p->nf_active;
+    g.wait_probe = p->wait_probe;
     if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
     if (p->gemm_adj == MDC_GEMM_GEMV && gemv_supported(p->nv) && !recip && p->nf_active == 0 && nb <= 1024)
@@ -323,9 +339,8 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
     if (!std::isfinite(scale)) return MDC_ERR_INVALID_ARG;
     if (nt > 4096) return MDC_ERR_UNSUPPORTED;
     if (nfft == 0) {
-        nfft = 64;
-        while (nfft < 2 * nt - 1) nfft *= 2;
-    } else if (!is_pow2(nfft) || nfft < 2 * nt - 1 || nfft < 64 || nfft > 8192) {
+        nfft = default_nfft(nt);
+    } else if (!nfft_supported(nfft) || nfft < 2 * nt - 1) {
         return MDC_ERR_UNSUPPORTED;
     }
     if (nb_max == 0) nb_max = ns;
@@ -568,10 +583,17 @@ int smdd_lsqr(mdc_plan_t p, float *X, const float *U_obs, int n_iter, int flags,
 
 namespace {
 
-// One step; SGD when vel is null, N-SGD otherwise; mute: causality table or null.  Arguments checked
-// by the callers.
+// Adam state of one step (Kingma & Ba, Algorithm 1): moments m, v and the scalars of step t
+struct AdamArgs {
+    float *m = nullptr, *v = nullptr;
+    float beta1 = 0.f, beta2 = 0.f, eps = 0.f, c1 = 1.f, c2 = 1.f;
+};
+
+// One step; SGD when vel and adam.m are null, N-SGD with vel, Adam with adam.m; mute: causality table or
+// null.  Arguments checked by the callers.
 int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, int nb, float alpha, int flags,
-              float *vel, float mu, const int32_t *mute, double *loss, cudaStream_t st) {
+              float *vel, float mu, const int32_t *mute, double *loss, cudaStream_t st,
+              const AdamArgs &adam = AdamArgs()) {
     int rc = MDC_OK;
     const bool recip = flags & SMDD_RECIPROCITY;
     // a1: model spectra (or the ones left by the previous step's fused update)
@@ -607,17 +629,25 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         // the momentum / mute update exists for the default radix order only: lay its grid out (and take
         // its twiddle table) for FFT variant 0, whatever the plan's variant
         const int v_plan = p->fft_variant;
-        if (vel || mute) p->fft_variant = 0;
+        if (vel || mute || adam.m) p->fft_variant = 0;
         FftArgs a = base_fft(p);
         a.g = model_grid(p, p->nv);
         p->fft_variant = v_plan;
         a.tout = X;
-        a.vec = vec4_ok(p->nt, X) && (vel == nullptr || vec4_ok(p->nt, vel));
+        a.vec = vec4_ok(p->nt, X) && (vel == nullptr || vec4_ok(p->nt, vel)) &&
+                (adam.m == nullptr || (vec4_ok(p->nt, adam.m) && vec4_ok(p->nt, adam.v)));
         a.spec = p->Xh;
         a.alpha = alpha;
         a.vel = vel;
         a.mu = mu;
         a.mute = mute;
+        a.adam_m = adam.m;
+        a.adam_v = adam.v;
+        a.beta1 = adam.beta1;
+        a.beta2 = adam.beta2;
+        a.eps = adam.eps;
+        a.c1 = adam.c1;
+        a.c2 = adam.c2;
         if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;
         if (keep) p->xhat_for = X;
     }
@@ -667,20 +697,20 @@ int smdd_step_host(mdc_plan_t p, float *X, const float *U_host, const int32_t *i
     memcpy(h.idx_pinned[s], idx_host, (size_t)nb * sizeof(int32_t));
     // the device slot is free once the step that used it two calls back has finished
     if (cudaStreamWaitEvent(h.copy, h.consumed[s], 0) != cudaSuccess) return MDC_ERR_CUDA;
-    if (cudaMemcpyAsync(h.idx[s], h.idx_pinned[s], (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice, h.copy) !=
-        cudaSuccess)
-        return MDC_ERR_CUDA;
+    // from the first copy on, every return marks the copies queued so far: the next use of this slot
+    // waits for them before it overwrites the pinned index list they read
+    bool queued = cudaMemcpyAsync(h.idx[s], h.idx_pinned[s], (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                  h.copy) == cudaSuccess;
     const size_t row = (size_t)p->nv * p->nt;
-    for (int b = 0; b < nb;) {
+    for (int b = 0; queued && b < nb;) {
         int e = b + 1;
         while (e < nb && idx_host[e] == idx_host[e - 1] + 1) ++e;   // consecutive sources: one copy
-        if (cudaMemcpyAsync(h.U[s] + (size_t)b * row, U_host + (size_t)idx_host[b] * row, (size_t)(e - b) * row * sizeof(float),
-                            cudaMemcpyHostToDevice, h.copy) != cudaSuccess)
-            return MDC_ERR_CUDA;
+        queued = cudaMemcpyAsync(h.U[s] + (size_t)b * row, U_host + (size_t)idx_host[b] * row,
+                                 (size_t)(e - b) * row * sizeof(float), cudaMemcpyHostToDevice, h.copy) == cudaSuccess;
         b = e;
     }
-    if (cudaEventRecord(h.copied[s], h.copy) != cudaSuccess || cudaStreamWaitEvent(st, h.copied[s], 0) != cudaSuccess)
-        return MDC_ERR_CUDA;
+    const bool recorded = cudaEventRecord(h.copied[s], h.copy) == cudaSuccess;
+    if (!queued || !recorded || cudaStreamWaitEvent(st, h.copied[s], 0) != cudaSuccess) return MDC_ERR_CUDA;
     rc = step_impl(p, X, h.U[s], h.idx[s], nb, prm->alpha, flags | SMDD_UOBS_GATHERED, nullptr, 0.f, nullptr,
                    loss_host ? h.loss[s] : nullptr, st);
     if (rc == MDC_OK && loss_host &&
@@ -697,26 +727,47 @@ int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx,
     if (rc) return rc;
     if (!prm) return MDC_ERR_INVALID_ARG;
     const int flags = prm->flags;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_NESTEROV))
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_NESTEROV | SMDD_ADAM))
         return MDC_ERR_INVALID_ARG;
-    if (prm->reserved0 != 0) return MDC_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
-        if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
+    if (prm->reserved != 0) return MDC_ERR_INVALID_ARG;
     if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
-    const bool nesterov = flags & SMDD_NESTEROV;
+    const bool nesterov = flags & SMDD_NESTEROV, adam = flags & SMDD_ADAM;
+    if (nesterov && adam) return MDC_ERR_INVALID_ARG;
     if (nesterov && (!prm->V || !(prm->mu >= 0.f && prm->mu < 1.f))) return MDC_ERR_INVALID_ARG;
-    if (!nesterov && prm->V) return MDC_ERR_INVALID_ARG;
+    if (adam && (!prm->V || !prm->S || prm->V == prm->S || prm->S == X || prm->t < 1 ||
+                 !(prm->beta1 >= 0.f && prm->beta1 < 1.f) || !(prm->beta2 >= 0.f && prm->beta2 < 1.f) ||
+                 !(prm->eps > 0.f) || !std::isfinite(prm->eps)))
+        return MDC_ERR_INVALID_ARG;
+    if (!nesterov && !adam && prm->V) return MDC_ERR_INVALID_ARG;
+    if (!adam && (prm->S || prm->t != 0)) return MDC_ERR_INVALID_ARG;
     if (prm->V == X) return MDC_ERR_INVALID_ARG;
     if ((flags & SMDD_RECIPROCITY) && p->nr != p->nv) return MDC_ERR_SHAPE;
+    AdamArgs ad;
+    if (adam) {
+        ad.m = prm->V;
+        ad.v = prm->S;
+        ad.beta1 = prm->beta1;
+        ad.beta2 = prm->beta2;
+        ad.eps = prm->eps;
+        // bias corrections 1 / (1 - beta^t), formed in double and rounded once
+        ad.c1 = (float)(1.0 / (1.0 - std::pow((double)prm->beta1, (double)prm->t)));
+        ad.c2 = (float)(1.0 / (1.0 - std::pow((double)prm->beta2, (double)prm->t)));
+    }
     DeviceGuard dg(p->device);
-    return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags & ~SMDD_NESTEROV, nesterov ? prm->V : nullptr,
-                     nesterov ? prm->mu : 0.f, prm->mute, loss, (cudaStream_t)stream);
+    return step_impl(p, X, U_obs, idx, nb, prm->alpha, flags & ~(SMDD_NESTEROV | SMDD_ADAM), nesterov ? prm->V : nullptr,
+                     nesterov ? prm->mu : 0.f, prm->mute, loss, (cudaStream_t)stream, ad);
 }
 
 int mdc_plan_set_band(mdc_plan_t p, int nf_active) {
     if (!p || nf_active < 0) return MDC_ERR_INVALID_ARG;
     p->nf_active = (nf_active == 0 || nf_active >= p->nf) ? 0 : nf_active;
     p->xhat_for = nullptr;
+    return MDC_OK;
+}
+
+int mdc_plan_set_wait_probe(mdc_plan_t p, long long cycles) {
+    if (!p || cycles < 0 || cycles > 100000000LL) return MDC_ERR_INVALID_ARG;
+    p->wait_probe = cycles;
     return MDC_OK;
 }
 

@@ -337,9 +337,14 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
             }
     } else {
         // causality mute (the step is zero before the first kept sample) and, with a velocity,
-        // Nesterov momentum on the look-ahead point: V <- mu V + step, X <- X + mu V + step
+        // Nesterov momentum on the look-ahead point: V <- mu V + step, X <- X + mu V + step;
+        // or, with Adam moments m and v (Kingma & Ba, Algorithm 1) of the preconditioned gradient g:
+        // m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, X <- X - alpha (c1 m) / (sqrt(c2 v) + eps)
         const int first = (a.mute && c.valid) ? __ldg(a.mute + (long long)c.j * a.g.ni + c.i) : 0;
-        float *vp = (a.vel && c.valid) ? a.vel + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : nullptr;
+        const long long toff = c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0;
+        float *vp = (a.vel && c.valid) ? a.vel + toff : nullptr;
+        float *mp = (a.adam_m && c.valid) ? a.adam_m + toff : nullptr;
+        float *sp = (a.adam_v && c.valid) ? a.adam_v + toff : nullptr;
 #pragma unroll
         for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
@@ -350,21 +355,35 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
                 const float4 xv = xo[hs];
                 const float gk[4] = {g0.x, g0.y, g1.x, g1.y}, xk[4] = {xv.x, xv.y, xv.z, xv.w};
                 float4 vv = vp ? load_quad(vp, i0, a.nt, a.vec) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float vk[4] = {vv.x, vv.y, vv.z, vv.w}, zk[4];
+                float4 mv = mp ? load_quad(mp, i0, a.nt, a.vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 sv = sp ? load_quad(sp, i0, a.nt, a.vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float vk[4] = {vv.x, vv.y, vv.z, vv.w}, mk[4] = {mv.x, mv.y, mv.z, mv.w};
+                float sk[4] = {sv.x, sv.y, sv.z, sv.w}, zk[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float st = (i0 + k >= first) ? nas * gk[k] : 0.f;
-                    if (vp) {
-                        vk[k] = fmaf(a.mu, vk[k], st);
-                        zk[k] = fmaf(a.mu, vk[k], xk[k] + st);
+                    if (mp) {
+                        const float g = (i0 + k >= first) ? a.s * gk[k] : 0.f;
+                        mk[k] = fmaf(a.beta1, mk[k], (1.f - a.beta1) * g);
+                        sk[k] = fmaf(a.beta2, sk[k], (1.f - a.beta2) * (g * g));
+                        zk[k] = xk[k] - a.alpha * (mk[k] * a.c1) / (sqrtf(sk[k] * a.c2) + a.eps);
                     } else {
-                        zk[k] = xk[k] + st;
+                        const float st = (i0 + k >= first) ? nas * gk[k] : 0.f;
+                        if (vp) {
+                            vk[k] = fmaf(a.mu, vk[k], st);
+                            zk[k] = fmaf(a.mu, vk[k], xk[k] + st);
+                        } else {
+                            zk[k] = xk[k] + st;
+                        }
                     }
                     if (i0 + k >= a.nt) zk[k] = 0.f;
                 }
                 const float4 z = make_float4(zk[0], zk[1], zk[2], zk[3]);
                 if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
                 if (vp) store_quad(vp, i0, a.nt, a.vec, make_float4(vk[0], vk[1], vk[2], vk[3]));
+                if (mp) {
+                    store_quad(mp, i0, a.nt, a.vec, make_float4(mk[0], mk[1], mk[2], mk[3]));
+                    store_quad(sp, i0, a.nt, a.vec, make_float4(sk[0], sk[1], sk[2], sk[3]));
+                }
                 xo[hs] = z;
             }
     }
@@ -502,6 +521,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
         case 256: { constexpr int MM = 256; __VA_ARGS__; } break;   \
         case 512: { constexpr int MM = 512; __VA_ARGS__; } break;   \
         case 1024: { constexpr int MM = 1024; __VA_ARGS__; } break; \
+        case 1536: { constexpr int MM = 1536; __VA_ARGS__; } break; \
         case 2048: { constexpr int MM = 2048; __VA_ARGS__; } break; \
         case 4096: { constexpr int MM = 4096; __VA_ARGS__; } break; \
         default: return cudaErrorInvalidValue;                    \
@@ -523,6 +543,7 @@ int fft_traces_per_cta(int M) {
         case 256: return Team<256>::TR;
         case 512: return Team<512>::TR;
         case 1024: return Team<1024>::TR;
+        case 1536: return Team<1536>::TR;
         case 2048: return Team<2048>::TR;
         case 4096: return Team<4096>::TR;
     }
@@ -537,6 +558,7 @@ int fft_blocks(int M, const TraceGrid &g) {
         case 256: return blocks_for<256>(g);
         case 512: return blocks_for<512>(g);
         case 1024: return blocks_for<1024>(g);
+        case 1536: return blocks_for<1536>(g);
         case 2048: return blocks_for<2048>(g);
         case 4096: return blocks_for<4096>(g);
     }
@@ -551,6 +573,7 @@ int fft_tw_size(int M, int v) {
         case 256: return tw_size(256, v);
         case 512: return tw_size(512, v);
         case 1024: return tw_size(1024, v);
+        case 1536: return tw_size(1536, v);
         case 2048: return tw_size(2048, v);
         case 4096: return tw_size(4096, v);
     }
@@ -681,15 +704,16 @@ static bool launch_update_pf(bool keep, const FftArgs &a, int ntiles, cudaStream
 }
 
 cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
-    if (a.variant == 2 && !a.vel && !a.mute) return launch2_update(M, keep, a, st);
+    const bool ext = a.vel || a.mute || a.adam_m;
+    if (a.variant == 2 && !ext) return launch2_update(M, keep, a, st);
     SMDD_SWITCH_M(M, {
         const int nb = blocks_for<MM>(a.g);
         if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
-        if (a.prefetch && !a.vel && !a.mute && launch_update_pf<MM>(keep, a, nb, st)) {
+        if (a.prefetch && !ext && launch_update_pf<MM>(keep, a, nb, st)) {
             // persistent, prefetching form launched
-        } else if (a.vel || a.mute) {
-            // momentum / causality mute: radix order 0 only (the caller passes its twiddle table)
+        } else if (ext) {
+            // momentum / Adam / causality mute: radix order 0 only (the caller passes its twiddle table)
             if (a.variant != 0) return cudaErrorInvalidValue;
             if (keep) k_update<MM, 0, true, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);
             else k_update<MM, 0, false, true><<<nb, Team<MM>::THREADS, Team<MM>::SMEM, st>>>(a);

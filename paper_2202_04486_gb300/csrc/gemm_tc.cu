@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int drows[NB];
-    __shared__ int fail;
+    __shared__ int fail, issued;
     uint8_t *sm = align1024(tc_raw);
     const int f = blockIdx.z, v0 = blockIdx.x * 128, b0 = blockIdx.y * NB;
     if (a.nf_active > 0 && f >= a.nf_active) {   // above the band limit: zero products, no TMEM
@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fail = 0;
+        issued = 0;
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
@@ -130,8 +131,14 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
     constexpr uint32_t idp = umma_idesc(128, NB, 0, 0, 0), idn = umma_idesc(128, NB, 0, 0, 1);
+    // failure-path check: before any copy or product, wait on a barrier that nothing arrives on (phase
+    // 0 of bars[1] never completes here) for a short limit, then take the timeout path below
+    if (a.wait_probe > 0) {
+        if (tid == 0 && !mbar_wait_limit(&bars[1], 0, a.wait_probe)) fail = 1;
+        __syncthreads();
+    }
 
-    const int nk = (a.nr + 63) / 64;
+    const int nk = fail ? 0 : (a.nr + 63) / 64;
     for (int kc = 0; kc < nk; ++kc) {
         const int s = kc % NSTAGE;
         uint8_t *st = sm + s * G::STAGE;
@@ -177,6 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
                 mma_complex_split(tmem, tmem + NB, ad, bd, idp, idn, (kc > 0 || ks > 0) ? 1u : 0u);
             }
             umma_commit(&bars[s]);
+            issued = 1;
         }
     }
     const int last = nk - 1;
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     __syncthreads();
     const bool ok = !fail;
     // after a timeout, give products still in flight one more bounded wait before TMEM is freed
-    if (!ok) mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1);
+    if (!ok && issued) mbar_wait_bounded(&bars[last % NSTAGE], (last / NSTAGE) & 1);
     tc_fence_after();
     __syncthreads();
     // epilogue: TMEM -> shared staging [128][NB] complex -> coalesced rows of C
@@ -251,10 +259,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
     using G = TcAdj;
     constexpr int KC = G::KC;
     extern __shared__ uint8_t tc_raw[];
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bar, probe_bar;
     __shared__ uint32_t tmem_holder;
     __shared__ int sidx[1024];
-    __shared__ int fail;
+    __shared__ int fail, issued;
     uint8_t *sm = align1024(tc_raw);
     uint8_t *sA = sm, *sB = sm + 4 * G::PLANE;
     float2 *stg = reinterpret_cast<float2 *>(sm + G::OPER);
@@ -289,7 +297,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
     }
     if (tid == 0) {
         mbar_init(&bar, 1);
+        mbar_init(&probe_bar, 1);
         fail = 0;
+        issued = 0;
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
@@ -298,10 +308,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
     constexpr uint32_t idp = umma_idesc(128, 128, 1, 1, 0), idn = umma_idesc(128, 128, 1, 1, 1);
+    // failure-path check: before any copy or product, wait on a barrier that nothing arrives on for a
+    // short limit, then take the timeout path below
+    if (a.wait_probe > 0) {
+        if (tid == 0 && !mbar_wait_limit(&probe_bar, 0, a.wait_probe)) fail = 1;
+        __syncthreads();
+    }
 
     const int nkc = (a.nb + KC - 1) / KC;
     const int nhalf = RECIP ? 2 : 1;
-    const int njobs = nkc * nhalf;
+    const int njobs = fail ? 0 : nkc * nhalf;
     constexpr int UD = KC * 16 / TC_THREADS;            // kernel-row units (8 complex) per thread
     int phase = 0;
     for (int job = 0; job < njobs; ++job) {
@@ -367,13 +383,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
                 mma_complex_split(tmem, tmem + 128, ad, bd, idp, idn, (job > 0 || ks > 0) ? 1u : 0u);
             }
             umma_commit(&bar);
+            issued = 1;
         }
     }
     if (!fail && !mbar_wait_bounded(&bar, phase & 1)) fail = 1;
     __syncthreads();
     const bool ok = !fail;
     // after a timeout, give products still in flight one more bounded wait before TMEM is freed
-    if (!ok) mbar_wait_bounded(&bar, phase & 1);
+    if (!ok && issued) mbar_wait_bounded(&bar, phase & 1);
     tc_fence_after();
     // epilogue in two passes of 64 columns: TMEM -> shared staging [128][65] -> coalesced rows (and
     // the mirror)

@@ -80,22 +80,20 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 extern "C" int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float *D, const float *X,
                                   const int32_t *idx, int nb, float *U, int *dev_status, void *stream) {
     using namespace smdd;
-    if (!D || !X || !idx || !U) return MDC_ERR_INVALID_ARG;
+    if (!D || !X || !idx || !U || !dev_status) return MDC_ERR_INVALID_ARG;
     if (nt < 1 || nr < 1 || nv < 1 || ns < 1 || nb < 1 || !std::isfinite(scale)) return MDC_ERR_INVALID_ARG;
     if (nt > 4096 || nb > 1024) return MDC_ERR_UNSUPPORTED;
-    int nfft = 64;
-    while (nfft < 2 * nt - 1) nfft *= 2;
+    const int nfft = default_nfft(nt);
     const int M = nfft / 2, nf = M + 1;
     const int ldr = (nr + 1) & ~1, ldb = (nb + 1) & ~1;
 
-    // scratch layout: twiddles | kernel spectra | model spectra | batch spectra | status word
+    // scratch layout: twiddles | kernel spectra | model spectra | batch spectra
     const size_t o_tw = 0;
     const size_t o_twn = align256(o_tw + (size_t)fft_tw_size(M) * sizeof(float2));
     const size_t o_dh = align256(o_twn + (size_t)(M + 1) * sizeof(float2));
     const size_t o_xh = align256(o_dh + (size_t)nf * ns * ldr * sizeof(float2));
     const size_t o_uh = align256(o_xh + (size_t)nf * nv * ldr * sizeof(float2));
-    const size_t o_st = align256(o_uh + (size_t)nf * nv * ldb * sizeof(float2));
-    const size_t need = o_st + 256;
+    const size_t need = align256(o_uh + (size_t)nf * nv * ldb * sizeof(float2));
     if (need > kScratchBytes) {   // the problem does not fit the static scratch
         fprintf(stderr, "mdc_forward_static: this problem needs %zu bytes of scratch; the static scratch holds %zu\n",
                 need, kScratchBytes);
@@ -114,7 +112,7 @@ extern "C" int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, c
     float2 *Dh = reinterpret_cast<float2 *>(base + o_dh);
     float2 *Xh = reinterpret_cast<float2 *>(base + o_xh);
     float2 *Uh = reinterpret_cast<float2 *>(base + o_uh);
-    int *status = dev_status ? dev_status : reinterpret_cast<int *>(base + o_st);
+    int *status = dev_status;   // the caller's word: index errors are always reported
 
     const int ntw = fft_tw_size(M);
     k_fill_twiddles<<<(ntw + M + 1 + 255) / 256, 256, 0, st>>>(tw, ntw, twN, M);

@@ -8,9 +8,12 @@
 // and back through the matching pre-processing and an inverse complex FFT of length M.
 //
 // A "team" of T = M/P threads owns one trace; each thread holds P complex values in registers.
-// The complex FFT is a self-sorting Stockham factorisation M = R_1 R_2 ... R_m (radices <= P, fixed
-// at compile time): pass p with radix R and span Ns = R_1...R_{p-1} maps butterfly j (inputs
-// j + r M/R) to outputs (j - j%Ns) R + j%Ns + r Ns after the twiddles w_{Ns R}^{r (j%Ns)}.  Between
+// The complex FFT is a self-sorting Stockham factorisation M = R_1 R_2 ... R_m (radices 3, 4 or 8,
+// fixed at compile time): pass p with radix R and span Ns = R_1...R_{p-1} maps butterfly j (inputs
+// j + r M/R) to outputs (j - j%Ns) R + j%Ns + r Ns after the twiddles w_{Ns R}^{r (j%Ns)}.  Lengths
+// M = 2^k use radices 4 and 8; M = 1536 (FFT length 3072, the shortest 3-smooth length >= 2 nt - 1 for
+// nt in 1025 .. 1536) adds one radix-3 pass in the middle of the plan, which moves its values through
+// shared memory on its own (512 butterflies over the 96 threads of a team).  Between
 // passes the values go through shared memory; the float2 index is XOR-swizzled within 16-element
 // groups so that both the contiguous reads and the strided writes of a half-warp hit distinct banks.
 // The first forward pass reads its inputs straight from registers (global loads or the output of a
@@ -92,6 +95,19 @@ __device__ __forceinline__ void dft8(float2 *a) {
     a[7] = csub(e3, o3);
 }
 
+// radix-3 DFT: y0 = a0 + a1 + a2, y1/2 = a0 - (a1 + a2)/2 -/+ i (sqrt(3)/2) (a1 - a2) (forward roots
+// w_3 = exp(-2 pi i / 3); the signs of the imaginary term swap for INV)
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 &a0, float2 &a1, float2 &a2) {
+    constexpr float h = 0.86602540378443864676f;   // sqrt(3) / 2
+    const float2 s = cadd(a1, a2), d = csub(a1, a2);
+    const float2 m = make_float2(fmaf(-0.5f, s.x, a0.x), fmaf(-0.5f, s.y, a0.y));
+    const float2 q = mul_mi<INV>(make_float2(h * d.x, h * d.y));   // -i h d (forward), +i h d (inverse)
+    a0 = cadd(a0, s);
+    a1 = cadd(m, q);
+    a2 = csub(m, q);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dftR(float2 *a) {
     if constexpr (R == 2) dft2<INV>(a[0], a[1]);
@@ -102,11 +118,13 @@ __device__ __forceinline__ void dftR(float2 *a) {
 
 // ------------------------------------------------------------------------------------------------
 // FFT plans: forward radix of pass p for complex length M (the inverse uses the radices in reverse
-// order).  Every radix is 4 or 8, so a thread's 16 values always form at least two butterflies.
+// order).  Radices 4 and 8 take a thread's 16 values as two or more butterflies; a radix-3 pass runs
+// through pass3_smem instead.
 // ------------------------------------------------------------------------------------------------
 constexpr int FFT_P = 16;   // complex values per thread
 
 __host__ __device__ constexpr int fft_npass(int M) { return M <= 64 ? 2 : M <= 512 ? 3 : 4; }
+__host__ __device__ constexpr bool is_pow2c(int x) { return x > 0 && (x & (x - 1)) == 0; }
 // variant 0: the default radix order; variant 1: the same radices in reverse order (identical to
 // variant 0 where every radix is 8).  Both are valid Stockham plans; which one is faster for a given
 // shape is left to measurement (the plan autotuner).
@@ -118,6 +136,7 @@ __host__ __device__ constexpr int fft_radix0(int M, int p) {
          : M == 512 ? 8
          : M == 1024 ? (p < 2 ? 8 : 4)
          : M == 2048 ? (p == 3 ? 4 : 8)
+         : M == 1536 ? (p == 2 ? 3 : 8)    // 8 * 8 * 3 * 8: the radix-3 pass is never the first or last
          : 8;  // 4096
 }
 __host__ __device__ constexpr int fft_radix(int M, int p, int v = 0) {
@@ -170,6 +189,12 @@ __host__ __device__ constexpr int padi(int i) { return i + 2 * (i >> 4); }
 #ifndef SMDD_FFT_MIN_TR              // fewest traces per CTA for M <= 1024
 #define SMDD_FFT_MIN_TR 2
 #endif
+#ifndef SMDD_FFT_TR_2048             // traces per CTA at M = 2048 (teams of 128 threads)
+#define SMDD_FFT_TR_2048 8
+#endif
+#ifndef SMDD_FFT_TR_1536             // traces per CTA at M = 1536 (teams of 96 threads)
+#define SMDD_FFT_TR_1536 4
+#endif
 #ifndef SMDD_FFT_NAMED_BAR           // 1: teams of more than one warp sync on their own named barrier
 #define SMDD_FFT_NAMED_BAR 1
 #endif
@@ -183,7 +208,7 @@ struct Team {
     // spectra, so small TR wastes sectors; at M = 2048 the CTA takes as many traces as 1024 threads
     // hold (8: 64-byte rows; measured 1.5x faster than 2 traces despite 64 registers per thread), else
     // at least SMDD_FFT_MIN_TR; at most 1024 threads
-    static constexpr int TR_MIN = M == 2048 ? 1024 / T : SMDD_FFT_MIN_TR;
+    static constexpr int TR_MIN = M == 2048 ? SMDD_FFT_TR_2048 : M == 1536 ? SMDD_FFT_TR_1536 : SMDD_FFT_MIN_TR;
     static constexpr int TR_LO = TR_RAW < TR_MIN ? TR_MIN : TR_RAW;
     static constexpr int TR = T * TR_LO > 1024 ? 1024 / T : TR_LO;
     static constexpr int THREADS = T * TR;                    // CTA size
@@ -259,7 +284,8 @@ __device__ __forceinline__ void pass_compute(float2 (&a)[FFT_P], int t, const fl
     for (int qq = 0; qq < QQ; ++qq) {
         if constexpr (NS > 1) {
             // butterflies j and j+1 use twiddle columns k0 and k0+1, adjacent in each row of the table
-            const int k0 = (2 * t + 2 * T * qq) & (NS - 1);
+            // (NS is even, so j and j+1 share the block of NS)
+            const int k0 = is_pow2c(NS) ? ((2 * t + 2 * T * qq) & (NS - 1)) : ((2 * t + 2 * T * qq) % NS);
             const float4 v1 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 1 * NS + k0));
             float4 v4 = v1;
             if constexpr (R == 8) v4 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 4 * NS + k0));
@@ -281,7 +307,18 @@ __device__ __forceinline__ void pass_compute(float2 (&a)[FFT_P], int t, const fl
 template <int M, int R, int NS>
 __device__ __forceinline__ void pass_store(float2 *buf, int t, const float2 (&a)[FFT_P]) {
     constexpr int T = M / FFT_P, QQ = FFT_P / R / 2;
-    if constexpr (NS == 1) {
+    if constexpr (!is_pow2c(NS)) {
+        static_assert((2 * T) % NS == 0, "the butterflies j0 + 2T qq share the residue of j0");
+        // spans with a factor 3: the padded index of every store is formed in full (the per-thread base
+        // plus immediate split needs power-of-two blocks); pairs stay 16-byte aligned (j even, NS even)
+        const int j0 = 2 * t, k = j0 % NS;
+#pragma unroll
+        for (int qq = 0; qq < QQ; ++qq) {
+            const int o = (j0 + 2 * T * qq - k) * R + k;   // j0 + 2T qq has the same residue k (2T % NS == 0)
+#pragma unroll
+            for (int r = 0; r < R; ++r) sts4(buf + padi(o + r * NS), a[(2 * qq) * R + r], a[(2 * qq + 1) * R + r]);
+        }
+    } else if constexpr (NS == 1) {
         float2 *b = buf + padi(2 * t * R);
 #pragma unroll
         for (int qq = 0; qq < QQ; ++qq)
@@ -309,18 +346,59 @@ __device__ __forceinline__ void pass_store(float2 *buf, int t, const float2 (&a)
     }
 }
 
+// A radix-3 pass of span NS, shared memory to shared memory (never the first or last pass of a plan, so
+// no register hand-over): butterfly j = t + T q (q < ceil(M / 3T), the last round partial) reads
+// j + r M/3, applies w_{3 NS}^{r (j % NS)} (table rows 1 and 2), transforms and stores at
+// (j - j % NS) 3 + j % NS + r NS.  Team syncs between the loads and the stores and at the end.
+template <int M, bool INV, int NS, int TWOFF>
+__device__ __forceinline__ void pass3_smem(float2 *buf, int t, const float2 *__restrict__ tw) {
+    constexpr int T = M / FFT_P, NBF = M / 3, NQ = (NBF + T - 1) / T;
+    float2 x[NQ][3];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int j = t + T * q;
+        if (j < NBF) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) x[q][r] = buf[padi(j + r * NBF)];
+        }
+    }
+    team_sync<T>();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int j = t + T * q;
+        if (j < NBF) {
+            const int k = j % NS;
+            if constexpr (NS > 1) {
+                const float2 w1 = __ldg(tw + TWOFF + NS + k), w2 = __ldg(tw + TWOFF + 2 * NS + k);
+                x[q][1] = INV ? cmulc(x[q][1], w1) : cmul(x[q][1], w1);
+                x[q][2] = INV ? cmulc(x[q][2], w2) : cmul(x[q][2], w2);
+            }
+            dft3<INV>(x[q][0], x[q][1], x[q][2]);
+            const int o = (j - k) * 3 + k;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) buf[padi(o + r * NS)] = x[q][r];
+        }
+    }
+    team_sync<T>();
+}
+
 template <int M, bool INV, int p, int PEND, int V>
 __device__ __forceinline__ void passes_from(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw) {
     // passes p .. PEND-1 of a direction: load, compute, and (except for the last inverse pass) store
     if constexpr (p < PEND) {
         constexpr int R = dir_radix(M, INV, p, V), NS = dir_span(M, INV, p, V);
-        pass_load<M, R>(buf, t, a);
-        if constexpr (!INV) team_sync<M / FFT_P>();
-        pass_compute<M, R, NS, INV, tw_off(M, INV, p, V)>(a, t, tw);
-        if constexpr (!INV || p + 1 < fft_npass(M)) {
-            if constexpr (INV) team_sync<M / FFT_P>();
-            pass_store<M, R, NS>(buf, t, a);
-            team_sync<M / FFT_P>();
+        if constexpr (R == 3) {
+            static_assert(p > 0 && p + 1 < fft_npass(M), "the radix-3 pass sits inside the plan");
+            pass3_smem<M, INV, NS, tw_off(M, INV, p, V)>(buf, t, tw);
+        } else {
+            pass_load<M, R>(buf, t, a);
+            if constexpr (!INV) team_sync<M / FFT_P>();
+            pass_compute<M, R, NS, INV, tw_off(M, INV, p, V)>(a, t, tw);
+            if constexpr (!INV || p + 1 < fft_npass(M)) {
+                if constexpr (INV) team_sync<M / FFT_P>();
+                pass_store<M, R, NS>(buf, t, a);
+                team_sync<M / FFT_P>();
+            }
         }
         passes_from<M, INV, p + 1, PEND, V>(a, buf, t, tw);
     }

@@ -49,6 +49,10 @@ struct FftArgs {
     float *vel;
     float mu;
     const int32_t *mute;
+    // update: Adam moments (null for SGD / N-SGD), decay rates, epsilon and the bias corrections
+    // c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t) of step t
+    float *adam_m, *adam_v;
+    float beta1, beta2, eps, c1, c2;
     int prefetch;            // update: persistent CTAs prefetching the next tile's spectra (M <= 1024)
 };
 
@@ -63,6 +67,7 @@ struct GemmArgs {
     int tiles_v, tiles_r;    // adjoint tile grid
     int *status;
     int nf_active;           // band limit: bins f >= nf_active (when > 0) get zero products
+    long long wait_probe;    // tensor-core kernels: > 0 = failure-path check (mdc_plan_set_wait_probe), cycles
 };
 
 // Zero the output tile [r0, r0+nrows) x [c0, c0+ncols) of a CTA whose frequency bin lies above the
@@ -74,6 +79,10 @@ __device__ __forceinline__ void zero_tile(float2 *C, long long ld, int r0, int n
         if (r < rmax && c < cmax) C[(long long)r * ld + c] = make_float2(0.f, 0.f);
     }
 }
+
+// FFT lengths of the trace kernels: powers of two 64 .. 8192 and 3072 (api.cu)
+bool nfft_supported(int nfft);
+int default_nfft(int nt);   // the shortest supported length >= max(2 nt - 1, 64)
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rfft(int M, const FftArgs &a, cudaStream_t st);

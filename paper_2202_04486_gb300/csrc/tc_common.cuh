@@ -55,18 +55,23 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Wait for the given phase parity of an mbarrier, giving up after about a second of clock.
+// Wait for the given phase parity of an mbarrier, giving up after `limit` SM clock cycles.
 // Returns false on timeout (the caller records the error and finishes without the result).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, long long limit) {
     uint32_t done = 0;
     const long long t0 = clock64();
     while (!done) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-        if (!done && clock64() - t0 > 2000000000LL) return false;
+        if (!done && clock64() - t0 > limit) return false;
     }
     return true;
+}
+
+// the same with the production limit: about a second of clock
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_limit(bar, parity, 2000000000LL);
 }
 
 // Announce `bytes` of asynchronous copies on the mbarrier and arrive on it (one thread).

@@ -200,6 +200,8 @@ WORKLOADS = {
                                        n_multiples=4, noise=0.0, reciprocity=True),
     "smdd_nt1024_n301_ns401_nb32": dict(nt=1024, nr=301, nv=301, ns=401, nb=32, dx=20.0, n_reflectors=8,
                                         n_multiples=4, noise=0.0, reciprocity=False),
+    "smdd_nt1024_n301_ns401_nb64": dict(nt=1024, nr=301, nv=301, ns=401, nb=64, dx=20.0, n_reflectors=8,
+                                        n_multiples=4, noise=0.0, reciprocity=False),
     # one virtual source on a Volve-like line of 180 receivers and 110 sources (single-virtual-source MDD)
     "smdd_nt1024_nr180_nv1_ns110_nb16": dict(nt=1024, nr=180, nv=1, ns=110, nb=16, dx=25.0, n_reflectors=8,
                                              n_multiples=4, noise=0.05, reciprocity=False),

@@ -73,3 +73,30 @@ def test_alu_probe_argument_errors_without_launching(lib):
 
 def test_host_step_argument_errors_without_launching(lib):
     assert lib.smdd_step_host(None, None, None, None, 1, None, None, None) == binding.MDC_ERR_INVALID_ARG
+
+
+def test_forward_static_shapes_checked_before_any_launch():
+    """The allocation-free entry point has no plan to check shapes against: the binding rejects a
+    mis-shaped array (or a missing status word) with ValueError before the library or a GPU is touched."""
+    D = torch.zeros(5, 3, 8)
+    X = torch.zeros(4, 3, 8)
+    idx = torch.zeros(2, dtype=torch.int32)
+    status = torch.zeros(1, dtype=torch.int32)
+    bad = [
+        dict(U=torch.zeros(2, 4, 7), dev_status=status),     # U too short in time
+        dict(U=torch.zeros(3, 4, 8), dev_status=status),     # U rows != idx.numel()
+        dict(U=torch.zeros(2, 4, 8), dev_status=None),       # no status word
+    ]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            binding.mdc_forward_static(D, X, idx, **kw)
+    with pytest.raises(ValueError):
+        binding.mdc_forward_static(D, torch.zeros(4, 2, 8), idx, torch.zeros(2, 4, 8), dev_status=status)
+    with pytest.raises(ValueError):
+        binding.mdc_forward_static(D[0], X, idx, torch.zeros(2, 4, 8), dev_status=status)
+
+
+def test_forward_static_requires_status_word(lib):
+    import ctypes
+    p = ctypes.c_void_p(256)   # never dereferenced: the argument check comes first
+    assert lib.mdc_forward_static(8, 2, 2, 2, 1.0, p, p, p, 1, p, None, None) == binding.MDC_ERR_INVALID_ARG

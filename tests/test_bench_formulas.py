@@ -1,8 +1,9 @@
 """The algorithmic work that bench.py divides by time (the roofline numerators), checked against figures
 worked out independently of it: the per-step flops and compulsory bytes printed for the benchmark
-workloads (F_gemm = 16 nb nr nv nf, F_fft = 5 nfft log2(nfft) (nr nv + nb nv), bytes = X read + write,
-the gathered kernel spectra, the batch rows of U_obs, and the G round trip with reciprocity), to the
-three digits they are printed with, and the fused update kernel's bytes per launch worked by hand."""
+workloads (F_gemm = 16 nb nr nv nf, F_fft = 5 nfft log2(nfft) (nr nv + nb nv) with nfft the smallest
+2^a 3^b 5^c >= 2 nt - 1, bytes = X read + write, the gathered kernel spectra, the batch rows of U_obs,
+and the G round trip with reciprocity), to the digits they are printed with, and the fused update
+kernel's algorithmic and staged bytes per launch worked by hand."""
 import pytest
 
 import bench
@@ -13,9 +14,8 @@ PRINTED = {
     (512, 256, 256, 16, True): (8.61, 3.57, 562),
     (1024, 301, 301, 32, False): (47.5, 11.3, 861),
     (1024, 301, 301, 64, False): (95.1, 12.4, 979),
+    (1500, 1200, 1200, 32, False): (1107, 256, 18.0e3),
 }
-# (the 1500 x 1200^3 member is printed for nfft = 3000, a 2^a 3^b 5^c length; this implementation pads
-# to the power of two at or above 2 nt - 1, 4096 there, so its figures differ by design)
 
 
 @pytest.mark.parametrize("shape", list(PRINTED), ids=lambda s: "x".join(map(str, s)))
@@ -31,12 +31,15 @@ def test_step_work_matches_printed_figures(shape):
     assert bench.step_bytes_compulsory(nt, nr, nv, nb, recip) / 1e6 == pytest.approx(mb, rel=6e-3)
 
 
-def test_fft_length_is_the_power_of_two_at_or_above_2nt_minus_1():
-    assert [bench.nfft_for(nt) for nt in (128, 512, 513, 1024, 1500)] == [256, 1024, 2048, 2048, 4096]
+def test_fft_length_is_the_smallest_5_smooth_at_or_above_2nt_minus_1():
+    # 1080 = 2^3 3^3 5 (1025 .. 1079 all have a prime factor above 5); 3000 = 2^3 3 5^3
+    assert [bench.nfft_for(nt) for nt in (1, 128, 512, 513, 1024, 1500)] == [1, 256, 1024, 1080, 2048, 3000]
 
 
 def test_update_bytes_per_launch_by_hand():
-    # nt 512, 201 x 201: read the gradient spectra and write the model spectra (513 bins x 8 bytes each),
-    # read and write the model (512 x 4 bytes each), per model trace
+    # nt 512, 201 x 201: read and write the model (512 x 4 bytes each) per model trace; the staged pipeline
+    # adds the gradient spectra read and the model spectra written (513 bins x 8 bytes each)
     w = bench.kernel_work("update", 512, 201, 201, 16)
-    assert w["bytes"] == 201 * 201 * (513 * 8 * 2 + 512 * 4 * 2) == 497093904
+    assert w["bytes"] == 201 * 201 * 512 * 4 * 2 == 165482496
+    assert w["staged"] == 201 * 201 * 513 * 8 * 2
+    assert w["flops"] == 2 * 2.5 * 1024 * 10 * 201 * 201

@@ -47,8 +47,9 @@ def test_reference_arm_other_ranks_do_nothing():
     import bench
 
     class A:
-        steps, warmup, workload = 3, 3, bench.DEFAULT_WORKLOAD
+        steps, warmup, workload, batch_n, batch_largest = 3, 3, "smdd_nt512_n201_nb16_recip", 48, 1
     assert bench.run_reference(A(), rank=1, world=2, w=bench.workload_dims(A.workload)) is None
+    assert bench.run_reference_batch(A(), rank=1, world=2) is None
 
 
 def test_replicas_draw_independent_batches():

@@ -45,15 +45,17 @@ def _check(gpu, ref, what, rel=REL_L2, elem=ELEM):
 
 
 # every FFT length where the reversed radix order (variant 1) differs from the default (M = 32, 128,
-# 256, 1024, 2048) or the two-pass FFT (variant 2) exists (M = 128 .. 1024), ragged sizes, odd nt and
-# nt = 2 mod 4 (scalar time I/O)
+# 256, 1024, 1536, 2048) or the two-pass FFT (variant 2) exists (M = 128 .. 1024), ragged sizes, odd nt
+# and nt = 2 mod 4 (scalar time I/O)
 VARIANT_SHAPES = [
     (30, 7, 5, 9, 4),         # nfft 64
     (100, 37, 29, 41, 5),     # nfft 256
     (200, 12, 10, 14, 6),     # nfft 512
     (257, 17, 19, 23, 17),    # nfft 1024, odd nt
     (600, 20, 20, 20, 4),     # nfft 2048
-    (1500, 6, 5, 7, 3),       # nfft 4096
+    (1500, 6, 5, 7, 3),       # nfft 3072 (radix 8 * 8 * 3 * 8, reversed 8 * 3 * 8 * 8)
+    (1025, 9, 7, 8, 5),       # nfft 3072, odd nt
+    (1800, 6, 5, 7, 3),       # nfft 4096
     (130, 9, 9, 12, 7),       # nfft 512, scalar time I/O
     (1024, 33, 35, 40, 9),    # nfft 2048, nt = M: no zero padding inside the first half
 ]

@@ -54,7 +54,9 @@ SHAPES = [
     (33, 5, 7, 6, 9),            # nb > ns: duplicate sources
     (257, 17, 19, 23, 17),       # odd nt, nfft 1024, two batch tiles in the forward product
     (600, 20, 20, 20, 4),        # nfft 2048
-    (1500, 6, 5, 7, 3),          # nfft 4096
+    (1500, 6, 5, 7, 3),          # nfft 3072 (radix 8 * 8 * 3 * 8)
+    (1536, 5, 6, 4, 5),          # nfft 3072, nt = M: no zero padding inside the first half
+    (1800, 6, 5, 7, 3),          # nfft 4096
     (2500, 3, 2, 4, 2),          # nfft 8192
     (64, 70, 65, 80, 20),        # several 64x64 adjoint tiles, two forward batch tiles
     (16, 300, 260, 10, 3),       # nv > 256: two forward row blocks

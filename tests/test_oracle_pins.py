@@ -210,6 +210,22 @@ def test_sigma2_bounds_operator_norm():
     assert ratios[0] < ratios[1] < ratios[2] and ratios[2] > 0.95
 
 
+def test_sigma2_scaled_operator():
+    """With scale != 1 the operator is scale * P, so its squared norm is scale^2 times that of P: the
+    bound of the scaled dense operator (built here independently, scale inside every Toeplitz block) keeps
+    the same ratio to oracle.sigma2_max(D, scale=...) as at scale 1, and tightens the same way with a
+    long record.  A factor of scale instead of scale^2 moves the ratio by 0.7 and fails."""
+    rng_D = synth.random_traces((3, 2, 6), seed=62)
+    for scale in (0.7, 2.5):
+        D = np.zeros((3, 2, 96))
+        D[:, :, :6] = rng_D
+        A = _dense_operator(D, [0, 1, 2], nv=1, scale=scale)
+        s2_op = np.linalg.norm(A, 2) ** 2
+        s2_k = oracle.sigma2_max(D, scale=scale)
+        assert s2_op <= s2_k * (1 + 1e-12)
+        assert s2_op / s2_k > 0.95
+
+
 def test_sgd_full_batch_is_landweber_and_converges_to_lstsq():
     """Full-batch SGD with alpha < 2/sigma^2 is the Landweber iteration; from 0 on a consistent system it
     converges to the minimum-norm least-squares solution (numpy.linalg.lstsq on the dense operator)."""
@@ -354,6 +370,91 @@ def test_nsgd_full_batch_converges_to_min_norm_solution():
     for _ in range(3000):
         X, V, _ = oracle.nsgd_step(D, X, V, U, np.arange(ns), 0.5 / s2, 0.9)
     assert np.linalg.norm(X.ravel() - x_ls) <= 1e-6 * np.linalg.norm(x_ls)
+
+
+def test_adam_against_element_loop():
+    """Three Adam steps of the oracle against Kingma & Ba's Algorithm 1 written out element by element,
+    on a gradient taken from the dense Toeplitz operator (independent of the oracle's sums), with
+    reciprocity and a causality mute so that the preconditioned gradient is what the moments see."""
+    n, nt, ns = 3, 7, 4
+    D = synth.random_traces((ns, n, nt), 91)
+    Xt = synth.random_traces((n, n, nt), 92)
+    Xt = 0.5 * (Xt + Xt.transpose(1, 0, 2))
+    U = oracle.mdc_forward(D, Xt, np.arange(ns)) + 0.1 * synth.random_traces((ns, n, nt), 93)
+    first = np.array([[0, 2, 4], [2, 0, 1], [4, 1, 0]])
+    idx = np.array([3, 1])
+    A = _dense_operator(D, idx, n)
+    alpha, b1, b2, eps = 0.01, 0.8, 0.95, 1e-6
+    X, M, V = np.zeros((n, n, nt)), np.zeros((n, n, nt)), np.zeros((n, n, nt))
+    x, m, v = X.ravel().copy(), M.ravel().copy(), V.ravel().copy()
+    for t in range(1, 4):
+        g = (A.T @ (A @ x - U[idx].ravel())).reshape(n, n, nt)
+        g = 0.5 * (g + g.transpose(1, 0, 2))
+        g = g.ravel()
+        for j in range(x.size):
+            vv, rr, tt = np.unravel_index(j, (n, n, nt))
+            gj = 0.0 if tt < first[vv, rr] else g[j]
+            m[j] = b1 * m[j] + (1 - b1) * gj
+            v[j] = b2 * v[j] + (1 - b2) * gj * gj
+            mh = m[j] / (1 - b1 ** t)
+            vh = v[j] / (1 - b2 ** t)
+            x[j] = x[j] - alpha * mh / (math.sqrt(vh) + eps)
+        X, M, V, _ = oracle.adam_step(D, X, M, V, U, idx, alpha, t, beta1=b1, beta2=b2, eps=eps, recip=True, mute=first)
+        np.testing.assert_allclose(X.ravel(), x, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(M.ravel(), m, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(V.ravel(), v, rtol=1e-12, atol=1e-16)
+    # the model stays symmetric and zero above the mute
+    np.testing.assert_array_equal(X, X.transpose(1, 0, 2))
+    assert np.all(X[np.arange(nt)[None, None, :] < first[:, :, None]] == 0.0)
+
+
+def test_adam_first_step_has_size_alpha():
+    """From zero moments the bias corrections make the first step alpha * g / (|g| + eps): of size alpha
+    wherever |g| >> eps, whatever the scale of the gradient (a dropped correction gives (1-beta1)/sqrt(1-beta2))."""
+    nt, nr, nv, ns = 16, 3, 2, 5
+    D = 1e3 * synth.random_traces((ns, nr, nt), 94)
+    X = synth.random_traces((nv, nr, nt), 95)
+    U = synth.random_traces((ns, nv, nt), 96)
+    idx = np.array([0, 4])
+    g, _, _ = oracle.gradient(D, X, U, idx)
+    Xn, _, _, _ = oracle.adam_step(D, X, np.zeros_like(X), np.zeros_like(X), U, idx, 0.003, 1)
+    big = np.abs(g) > 1e3 * 1e-8
+    assert big.mean() > 0.9
+    np.testing.assert_allclose(np.abs(Xn - X)[big], 0.003, rtol=1e-5)
+    np.testing.assert_array_equal(np.sign(X - Xn)[big], np.sign(g)[big])
+
+
+def test_adam_without_averaging_is_sign_descent():
+    """beta1 = beta2 = 0: m_hat = g and v_hat = g^2 at every step, so Adam moves each element by
+    alpha * g / (|g| + eps), a signed step of size ~alpha."""
+    nt, nr, nv, ns = 9, 2, 2, 3
+    D = synth.random_traces((ns, nr, nt), 97)
+    X = synth.random_traces((nv, nr, nt), 98)
+    U = synth.random_traces((ns, nv, nt), 99)
+    M = synth.random_traces((nv, nr, nt), 100)
+    V = np.abs(synth.random_traces((nv, nr, nt), 101))
+    g, _, _ = oracle.gradient(D, X, U, [2, 0])
+    Xn, Mn, Vn, _ = oracle.adam_step(D, X, M, V, U, [2, 0], 0.1, 5, beta1=0.0, beta2=0.0, eps=1e-8)
+    np.testing.assert_allclose(Xn, X - 0.1 * g / (np.abs(g) + 1e-8), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(Mn, g, rtol=0, atol=0)
+    np.testing.assert_allclose(Vn, g * g, rtol=0, atol=0)
+
+
+def test_adam_full_batch_converges_to_least_squares():
+    """Full-batch Adam from zero with the decaying step alpha_t = 0.2 / sqrt(t) on a tiny consistent
+    over-determined problem (ns > nr: the dense operator has full column rank) converges to its unique
+    least-squares solution, the true model."""
+    nt, nr, nv, ns = 6, 2, 1, 5
+    D = synth.random_traces((ns, nr, nt), 11)
+    Xt = synth.random_traces((nv, nr, nt), 12)
+    U = oracle.mdc_forward(D, Xt, np.arange(ns))
+    A = _dense_operator(D, np.arange(ns), nv)
+    x_ls = np.linalg.lstsq(A, U.ravel(), rcond=None)[0]
+    assert np.linalg.matrix_rank(A) == A.shape[1]
+    X, M, V = np.zeros((nv, nr, nt)), np.zeros((nv, nr, nt)), np.zeros((nv, nr, nt))
+    for t in range(1, 3001):
+        X, M, V, _ = oracle.adam_step(D, X, M, V, U, np.arange(ns), 0.2 / math.sqrt(t), t)
+    assert np.linalg.norm(X.ravel() - x_ls) <= 1e-9 * np.linalg.norm(x_ls)
 
 
 def test_causal_mute_against_loop():
