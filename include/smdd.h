@@ -242,10 +242,11 @@ int mdc_forward_static(int nt, int nr, int nv, int ns, float scale, const float 
 
 typedef struct {
     int fft_variant;   /* 0: default radix order of the FFT plan; 1: the reversed order (accepted for
-                          every size, identical to 0 where all radices are equal); 2: the two-pass FFT
-                          (32 values per thread, one shared-memory exchange per transform; FFT lengths
-                          256 .. 2048, i.e. nfft/2 in 128 .. 1024; elsewhere 2 means 0).  Steps with
-                          N-SGD or the causality mute run variant 0 whatever is set. */
+                          every size, identical to 0 where all radices are equal); 2: the register FFT:
+                          two passes with 32 values per thread and one shared-memory exchange per
+                          transform for FFT lengths 256 .. 2048, three passes (48 * 4 * 8) with 48
+                          values per thread and two exchanges for 3072; elsewhere 2 means 0.  Steps
+                          with N-SGD, Adam or the causality mute run variant 0 whatever is set. */
     int gemm_fwd;      /* MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_GEMV or MDC_GEMM_TC_STREAM */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
     int fft_prefetch;  /* 1: the update runs as persistent CTAs that prefetch the next tile's gradient

@@ -378,7 +378,7 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         p->fft_variant = v_default;
     }
     bool ok = cudaMalloc(&p->Dh, szD) == cudaSuccess && cudaMalloc(&p->Xh, szX) == cudaSuccess &&
-              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw2_off + M + 2) * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&p->Uh, szU) == cudaSuccess && cudaMalloc(&p->tw, (size_t)(p->tw2_off + std::max(fft2_tw_size(M), M) + 2) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->twN, (M + 1) * sizeof(float2)) == cudaSuccess &&
               cudaMalloc(&p->partials, (size_t)(p->resid_blocks_max + 1) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&p->lam, (size_t)(nf + 1) * sizeof(double)) == cudaSuccess &&

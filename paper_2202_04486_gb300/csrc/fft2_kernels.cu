@@ -1,7 +1,9 @@
 // The trace kernels of fft_kernels.cu (rfft, irfft with window, residual step, update step) on the
-// two-pass FFT of smdd_fft2.cuh (radix-order variant 2, 128 <= M <= 1024).  Same arguments, same
-// results; a team of M/32 threads per trace, 32 values per thread, one shared-memory exchange per
-// transform, the real-signal post-processing through warp shuffles.
+// register FFTs of radix-order variant 2: the two-pass FFT of smdd_fft2.cuh (128 <= M <= 1024; a team of
+// M/32 threads per trace, 32 values per thread, one shared-memory exchange per transform) and the
+// three-pass FFT of smdd_fft3.cuh (M = 1536; a warp per trace, 48 values per thread, two exchanges).
+// Same arguments, same results as the radix kernels; the real-signal post-processing through warp
+// shuffles.
 //
 // Time samples: thread t of a team holds z[n] = (x[2n], x[2n+1]) for n = t + T m, so for every m the
 // team reads / writes 2T consecutive samples.
@@ -9,11 +11,44 @@
 #include <vector>
 
 #include "smdd_fft2.cuh"
+#include "smdd_fft3.cuh"
 #include "smdd_internal.h"
 
 namespace smdd {
 
 namespace {
+
+// Traits of the register FFTs: P values per thread, T threads per trace, TR traces per CTA; fwd / inv
+// run the real transforms between the registers (time samples z[n], n = t + T m, m < P / 2) and the
+// trace's shared-memory spectrum.  PREFETCH: the time-domain operand of the update / residual is loaded
+// into registers before the inverse transform (where the registers allow it), else right after it.
+template <int M>
+struct RegFft {
+    using F = Fft2<M>;
+    static constexpr int P = F::P, T = F::T, TR = F::TR, THREADS = F::THREADS, STRIDE = F::STRIDE;
+    static constexpr size_t SMEM = F::SMEM;
+    static constexpr bool PREFETCH = true;
+    __device__ static void fwd(float2 (&a)[P], float2 *buf, int t, const float2 *tw, const float2 *twN) {
+        rfft2_regs_to_smem<M>(a, buf, t, tw, twN);
+    }
+    __device__ static void inv(float2 (&a)[P], float2 *buf, int t, const float2 *tw, const float2 *twN) {
+        irfft2_smem_to_regs<M>(a, buf, t, tw, twN);
+    }
+};
+
+template <>
+struct RegFft<1536> {
+    using F = Fft3;
+    static constexpr int P = F::P, T = F::T, TR = F::TR, THREADS = F::THREADS, STRIDE = F::STRIDE;
+    static constexpr size_t SMEM = F::SMEM;
+    static constexpr bool PREFETCH = false;   // 48 values per thread already fill most of the registers
+    __device__ static void fwd(float2 (&a)[P], float2 *buf, int t, const float2 *tw, const float2 *twN) {
+        rfft3_regs_to_smem(a, buf, t, tw, twN);
+    }
+    __device__ static void inv(float2 (&a)[P], float2 *buf, int t, const float2 *tw, const float2 *twN) {
+        irfft3_smem_to_regs(a, buf, t, tw, twN);
+    }
+};
 
 struct TileCoord2 {
     int i, j;
@@ -22,7 +57,7 @@ struct TileCoord2 {
 
 template <int M>
 __device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr) {
-    constexpr int TR = Fft2<M>::TR;
+    constexpr int TR = RegFft<M>::TR;
     const int ti = 1 << g.ti_log2;
     const int tj = TR >> g.ti_log2;
     const int ntile_i = (g.ni + ti - 1) / ti;
@@ -38,7 +73,7 @@ __device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr) {
 // tr = tid % TR, bins f = tid / TR + it * (THREADS / TR)
 template <int M>
 __device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g) {
-    using F = Fft2<M>;
+    using F = RegFft<M>;
     constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
     const TileCoord2 c = coord2_of<M>(g, tr);
@@ -63,7 +98,7 @@ __device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict_
 
 template <int M>
 __device__ __forceinline__ void tile2_store(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g) {
-    using F = Fft2<M>;
+    using F = RegFft<M>;
     constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
     const TileCoord2 c = coord2_of<M>(g, tr);
@@ -99,38 +134,38 @@ __device__ __forceinline__ void store_z(float *y, int n, int nt, bool vec, float
 }
 
 template <int M>
-__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_rfft(FftArgs a) {
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_rfft(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
-    using F = Fft2<M>;
-    constexpr int T = F::T;
+    using F = RegFft<M>;
+    constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord2 c = coord2_of<M>(a.g, tr);
     float2 *buf = sm + tr * F::STRIDE;
     const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    float2 v[32];
+    float2 v[P];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = (m < 16 && c.valid) ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
-    rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    for (int m = 0; m < P; ++m) v[m] = (m < P / 2 && c.valid) ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    F::fwd(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile2_store<M>(sm, a.spec, a.g);
 }
 
 template <int M>
-__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_irfft_out(FftArgs a) {
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_irfft_out(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
-    using F = Fft2<M>;
-    constexpr int T = F::T;
+    using F = RegFft<M>;
+    constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     tile2_load<M>(sm, a.spec, a.g);
     __syncthreads();
     const TileCoord2 c = coord2_of<M>(a.g, tr);
     float2 *buf = sm + tr * F::STRIDE;
-    float2 v[32];
-    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    float2 v[P];
+    F::inv(v, buf, t, a.tw, a.twN);
     if (!c.valid) return;   // no barrier follows
     float *y = a.tout + (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) store_z(y, t + T * m, a.nt, a.vec, make_float2(v[m].x * a.s, v[m].y * a.s));
+    for (int m = 0; m < P / 2; ++m) store_z(y, t + T * m, a.nt, a.vec, make_float2(v[m].x * a.s, v[m].y * a.s));
 }
 
 __device__ __forceinline__ double block_sum2(double v, double *red) {
@@ -148,12 +183,12 @@ __device__ __forceinline__ double block_sum2(double v, double *red) {
 
 // residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], FP64 loss partials, Rh = rfft(R) in place
 template <int M>
-__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_residual(FftArgs a) {
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[32];
     __shared__ bool am_last;
-    using F = Fft2<M>;
-    constexpr int T = F::T;
+    using F = RegFft<M>;
+    constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord2 c = coord2_of<M>(a.g, tr);
     const float *uo = nullptr;
@@ -168,18 +203,24 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_residual(FftArgs a) {
         }
         if (row >= 0) uo = a.uobs + (long long)row * a.uo_si + (long long)c.j * a.uo_sj;
     }
-    float2 o[16];
+    float2 o[P / 2];
+    if constexpr (F::PREFETCH) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) o[m] = uo ? load_z(uo, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+        for (int m = 0; m < P / 2; ++m) o[m] = uo ? load_z(uo, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    }
     tile2_load<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * F::STRIDE;
-    float2 v[32];
-    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    float2 v[P];
+    F::inv(v, buf, t, a.tw, a.twN);
+    if constexpr (!F::PREFETCH) {
+#pragma unroll
+        for (int m = 0; m < P / 2; ++m) o[m] = uo ? load_z(uo, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    }
     double l2 = 0.0;
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-        if (m < 16) {
+    for (int m = 0; m < P; ++m) {
+        if (m < P / 2) {
             const int i0 = 2 * (t + T * m);
             float2 q = make_float2(0.f, 0.f);
             if (c.valid) {
@@ -192,7 +233,7 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_residual(FftArgs a) {
             v[m] = make_float2(0.f, 0.f);
         }
     }
-    rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+    F::fwd(v, buf, t, a.tw, a.twN);
     __syncthreads();
     tile2_store<M>(sm, a.spec, a.g);
 
@@ -219,25 +260,31 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_residual(FftArgs a) {
 
 // update step: g = s * irfft(Gh)[0:nt]; X <- X - alpha g; optionally Gh <- rfft(X_new) in place
 template <int M, bool KEEP>
-__global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_update(FftArgs a) {
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_update(FftArgs a) {
     extern __shared__ __align__(16) float2 sm[];
-    using F = Fft2<M>;
-    constexpr int T = F::T;
+    using F = RegFft<M>;
+    constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
     const TileCoord2 c = coord2_of<M>(a.g, tr);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    float2 xo[16];
+    float2 xo[P / 2];
+    if constexpr (F::PREFETCH) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) xo[m] = c.valid ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+        for (int m = 0; m < P / 2; ++m) xo[m] = c.valid ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    }
     tile2_load<M>(sm, a.spec, a.g);
     __syncthreads();
     float2 *buf = sm + tr * F::STRIDE;
-    float2 v[32];
-    irfft2_smem_to_regs<M>(v, buf, t, a.tw, a.twN);
+    float2 v[P];
+    F::inv(v, buf, t, a.tw, a.twN);
+    if constexpr (!F::PREFETCH) {
+#pragma unroll
+        for (int m = 0; m < P / 2; ++m) xo[m] = c.valid ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
+    }
     const float nas = -a.alpha * a.s;
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-        if (m < 16) {
+    for (int m = 0; m < P; ++m) {
+        if (m < P / 2) {
             const int n = t + T * m, i0 = 2 * n;
             float2 z;
             z.x = (i0 < a.nt) ? fmaf(nas, v[m].x, xo[m].x) : 0.f;
@@ -249,7 +296,7 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_update(FftArgs a) {
         }
     }
     if constexpr (KEEP) {
-        rfft2_regs_to_smem<M>(v, buf, t, a.tw, a.twN);
+        F::fwd(v, buf, t, a.tw, a.twN);
         __syncthreads();
         tile2_store<M>(sm, a.spec, a.g);
     }
@@ -258,7 +305,7 @@ __global__ void __launch_bounds__(Fft2<M>::THREADS, 2) k2_update(FftArgs a) {
 template <int M>
 int blocks2_for(const TraceGrid &g) {
     // -1: the grid was laid out for CTAs of another trace count (more traces along i than a CTA holds)
-    const int ti = 1 << g.ti_log2, tj = Fft2<M>::TR >> g.ti_log2;
+    const int ti = 1 << g.ti_log2, tj = RegFft<M>::TR >> g.ti_log2;
     if (tj < 1) return -1;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
 }
@@ -269,12 +316,13 @@ int blocks2_for(const TraceGrid &g) {
         case 256: { constexpr int MM = 256; __VA_ARGS__; } break;    \
         case 512: { constexpr int MM = 512; __VA_ARGS__; } break;    \
         case 1024: { constexpr int MM = 1024; __VA_ARGS__; } break;  \
+        case 1536: { constexpr int MM = 1536; __VA_ARGS__; } break;  \
         default: return cudaErrorInvalidValue;                       \
     }
 
 }  // namespace
 
-bool fft2_supported(int M) { return M >= 128 && M <= 1024; }
+bool fft2_supported(int M) { return (M >= 128 && M <= 1024) || M == 1536; }
 
 int fft2_traces_per_cta(int M) {
     switch (M) {
@@ -282,6 +330,7 @@ int fft2_traces_per_cta(int M) {
         case 256: return Fft2<256>::TR;
         case 512: return Fft2<512>::TR;
         case 1024: return Fft2<1024>::TR;
+        case 1536: return Fft3::TR;
     }
     return 0;
 }
@@ -292,24 +341,37 @@ int fft2_blocks(int M, const TraceGrid &g) {
         case 256: return blocks2_for<256>(g);
         case 512: return blocks2_for<512>(g);
         case 1024: return blocks2_for<1024>(g);
+        case 1536: return blocks2_for<1536>(g);
     }
     return 0;
 }
 
-// pass-2 table [r][j'] = w_M^{r j'} (r < M/32, j' < 32), double precision rounded once
+int fft2_tw_size(int M) { return M == 1536 ? Fft3::TW_SIZE : M; }
+
+// M <= 1024: the pass-2 table [r][j'] = w_M^{r j'} (r < M/32, j' < 32); M = 1536: the pass-2 table
+// [r][k] = w_192^{r k} (r < 4, k < 48) followed by the pass-3 table [r][j] = w_1536^{r j} (r < 8,
+// j < 192); double precision rounded once
 void fft2_tw_fill(int M, std::vector<float2> &tw) {
     const double pi = 3.14159265358979323846;
-    tw.assign(M, make_float2(0.f, 0.f));
+    tw.assign(fft2_tw_size(M), make_float2(0.f, 0.f));
+    auto put = [&](int i, long long num, long long den) {
+        const double ang = 2.0 * pi * (double)num / (double)den;
+        tw[i] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    };
+    if (M == 1536) {
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 48; ++k) put(r * 48 + k, (long long)r * k, 192);
+        for (int r = 0; r < 8; ++r)
+            for (int j = 0; j < 192; ++j) put(Fft3::TW2 + r * 192 + j, (long long)r * j, 1536);
+        return;
+    }
     for (int r = 0; r < M / 32; ++r)
-        for (int j = 0; j < 32; ++j) {
-            const double ang = 2.0 * pi * (double)(r * j) / (double)M;
-            tw[r * 32 + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
-        }
+        for (int j = 0; j < 32; ++j) put(r * 32 + j, (long long)r * j, M);
 }
 
 template <int M>
 static cudaError_t prepare2_m() {
-    const int sm = (int)Fft2<M>::SMEM;
+    const int sm = (int)RegFft<M>::SMEM;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_rfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_irfft_out<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -329,7 +391,7 @@ cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st) {
         const int nb = blocks2_for<MM>(a.g);
         if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
-        k2_rfft<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+        k2_rfft<MM><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
 }
@@ -339,7 +401,7 @@ cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st) {
         const int nb = blocks2_for<MM>(a.g);
         if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
-        k2_irfft_out<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+        k2_irfft_out<MM><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
 }
@@ -348,7 +410,7 @@ cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cuda
     SMDD_SWITCH_M2(M, {
         const int nb = blocks2_for<MM>(a.g);
         if (nb <= 0 || nb > nblocks_expected) return cudaErrorInvalidValue;
-        k2_residual<MM><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+        k2_residual<MM><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
 }
@@ -358,8 +420,8 @@ cudaError_t launch2_update(int M, bool keep, const FftArgs &a, cudaStream_t st) 
         const int nb = blocks2_for<MM>(a.g);
         if (nb < 0) return cudaErrorInvalidValue;
         if (nb == 0) return cudaSuccess;
-        if (keep) k2_update<MM, true><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
-        else k2_update<MM, false><<<nb, Fft2<MM>::THREADS, Fft2<MM>::SMEM, st>>>(a);
+        if (keep) k2_update<MM, true><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
+        else k2_update<MM, false><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
 }

@@ -192,8 +192,8 @@ __host__ __device__ constexpr int padi(int i) { return i + 2 * (i >> 4); }
 #ifndef SMDD_FFT_TR_2048             // traces per CTA at M = 2048 (teams of 128 threads)
 #define SMDD_FFT_TR_2048 8
 #endif
-#ifndef SMDD_FFT_TR_1536             // traces per CTA at M = 1536 (teams of 96 threads)
-#define SMDD_FFT_TR_1536 4
+#ifndef SMDD_FFT_TR_1536             // traces per CTA at M = 1536 (teams of 96 threads; 8 measured 1.2x
+#define SMDD_FFT_TR_1536 8           // faster than 4 on the update at nt 1500, 1200 x 200)
 #endif
 #ifndef SMDD_FFT_NAMED_BAR           // 1: teams of more than one warp sync on their own named barrier
 #define SMDD_FFT_NAMED_BAR 1

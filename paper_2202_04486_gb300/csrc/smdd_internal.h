@@ -96,11 +96,13 @@ int fft_tw_size(int M, int variant = 0);
 bool fft_has_variant(int M, int variant);                     // variant 1 exists where it differs from 0
 void fft_tw_fill(int M, std::vector<float2> &tw, int variant = 0);   // host: per-pass twiddle tables
 
-// two-pass FFT kernels (radix-order variant 2, 128 <= M <= 1024; fft2_kernels.cu)
+// register FFT kernels (radix-order variant 2: two passes for 128 <= M <= 1024, three for M = 1536;
+// fft2_kernels.cu)
 bool fft2_supported(int M);
 int fft2_traces_per_cta(int M);
 int fft2_blocks(int M, const TraceGrid &g);
-void fft2_tw_fill(int M, std::vector<float2> &tw);   // host: the pass-2 table, M entries
+int fft2_tw_size(int M);                             // entries of the variant's twiddle tables
+void fft2_tw_fill(int M, std::vector<float2> &tw);   // host: the variant's twiddle tables
 cudaError_t fft2_prepare(int M);
 cudaError_t launch2_rfft(int M, const FftArgs &a, cudaStream_t st);
 cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st);
