@@ -851,7 +851,8 @@ def run_gpu_batch(args, rank, world):
                           nfft_library=binding.mdc_plan_info(plan.handle)[0]))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
-    batch = binding.MDCBatch(members, n_branches=args.branches)
+    mode = binding.MDC_BATCH_QUEUE if args.batch_mode == "queue" else binding.MDC_BATCH_BRANCHES
+    batch = binding.MDCBatch(members, n_branches=args.branches, mode=mode)
     step_sizes = [(m["nt"], m["nr"], m["nv"], min(m["nb"], m["ns"] - s * m["nb"]), m["reciprocity"])
                   for m in setup for s in range(m["steps"])]
     epoch_flops = sum(step_flops(nt, nr, nv, nb) for nt, nr, nv, nb, _ in step_sizes)
@@ -944,6 +945,7 @@ def run_gpu_batch(args, rank, world):
                    "steps_per_epoch_all_members": sum(sp["steps"] for sp in setup), "nb": 32,
                    "precision": args.precision, "a_step_of_this_line": "one epoch of every member (one graph replay)",
                    "branches": batch.n_branches, "kernels_per_epoch": batch.kernels_per_epoch,
+                   "epoch_layout": args.batch_mode,
                    "autotuned": bool(args.autotune), "chosen_configs": cfgs,
                    "members_by_nt_nfft_algorithmic_library": nffts,
                    "l2": "inputs larger than L2 (no flush)", "setup_s": round(t_setup, 1),
@@ -967,8 +969,40 @@ def run_gpu_batch(args, rank, world):
         "wall_s_timed_region": round(wall, 3),
         "loss_first_last_sum": [sum(loss_first), sum(loss_last)],
     }
-    # release the members before the mixed-precision comparison
+    # the other epoch layout on the same members, timed the same way (a few epochs): the branch graph
+    # against the waves of persistent work-queue kernels
     batch.close()
+    other = binding.MDC_BATCH_BRANCHES if mode == binding.MDC_BATCH_QUEUE else binding.MDC_BATCH_QUEUE
+    try:
+        if other == binding.MDC_BATCH_QUEUE:   # the queue layout runs every product on the tile kernel
+            for m in members:
+                c = m["plan"].get_config()
+                if c["gemm_fwd"] == binding.MDC_GEMM_TC_STREAM:
+                    m["plan"].set_config(gemm_fwd=binding.MDC_GEMM_TC)
+        b2 = binding.MDCBatch(members, n_branches=args.branches, mode=other)
+        b2.run(0, 1)
+        k2 = min(args.steps, 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b2.run(1, k2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for m in members:
+            if m["plan"].sync_status() != binding.MDC_OK:
+                raise RuntimeError("device status after the other epoch layout")
+        t_other = e0.elapsed_time(e1) / k2
+        out["batch_layouts"] = {
+            "timed_layout": args.batch_mode, "timed_ms_per_epoch": round(ms_epoch, 3),
+            "other_layout": "queue" if other == binding.MDC_BATCH_QUEUE else "branches",
+            "other_ms_per_epoch": round(t_other, 3), "other_epochs_timed": k2,
+            "other_kernels_per_epoch": b2.kernels_per_epoch,
+            "definition": ("branches: every member's steps as its plan's own launches on parallel graph branches; "
+                           "queue: the epoch in waves (step w of every member), each stage one launch per kernel "
+                           "family of persistent CTAs taking (problem, tile) items from a device work queue")}
+        b2.close()
+    except binding.MDCError as e:
+        out["batch_layouts"] = {"timed_layout": args.batch_mode, "other_layout_error": str(e)}
+    # release the members before the mixed-precision comparison
     for m in members:
         m["plan"].close()
     members.clear()
@@ -1089,6 +1123,8 @@ def main():
     ap.add_argument("--batch-largest", type=int, default=1,
                     help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")
     ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
+    ap.add_argument("--batch-mode", default="branches", choices=["branches", "queue"],
+                    help=f"{BATCH_WORKLOAD}: epoch layout of the timed run (the other one is timed beside it)")
     ap.add_argument("--solver-epochs", type=int, default=0,
                     help="also compare SGD, N-SGD and full-gradient LSQR over this many epochs (model error per epoch)")
     ap.add_argument("--l2", default="auto", choices=["auto", "flush", "none"],

@@ -310,6 +310,23 @@ typedef struct {
  * stream orders the initialisation; the call returns after it is done.  Nothing runs on the members'
  * arrays until mdc_batch_run. */
 int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_branches, void *stream);
+
+/* The same with the layout of the epoch chosen by mode:
+ *   MDC_BATCH_BRANCHES : as mdc_batch_create (each member's steps as its plan's own launches, members on
+ *                        n_branches parallel graph branches);
+ *   MDC_BATCH_QUEUE    : persistent kernels with device work queues.  The epoch runs in waves, wave w
+ *                        holding step w of every member that has one (members have ceil(ns/nb) steps);
+ *                        each stage of a wave -- the model transform (wave 0), the forward product, the
+ *                        residual step, the adjoint product, the update -- is one launch per kernel family
+ *                        (FFT length and variant; product kernel) of CTAs resident on every SM, which take
+ *                        (problem, tile) items from a queue in device memory by atomic counter until it is
+ *                        empty.  The same steps and arithmetic as the branch layout (results equal bit for
+ *                        bit).  n_branches is ignored.  Every member's plan must be MDC_PREC_BF16X3 with
+ *                        tensor-core products (MDC_GEMM_TC or MDC_GEMM_TC_STREAM forward -- run on the tile
+ *                        kernel --, MDC_GEMM_TC adjoint) and no band limit, else MDC_ERR_UNSUPPORTED. */
+#define MDC_BATCH_BRANCHES 0
+#define MDC_BATCH_QUEUE    1
+int mdc_batch_create_ex(mdc_batch_t *out, const smdd_member *members, int n, int mode, int n_branches, void *stream);
 /* Run epochs first_epoch .. first_epoch + n_epochs - 1 of every member on stream (asynchronous). */
 int mdc_batch_run(mdc_batch_t batch, long long first_epoch, int n_epochs, void *stream);
 /* Kernel launches in one replay of the epoch graph, and the branch count (host pointers, may be NULL). */

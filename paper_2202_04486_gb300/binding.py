@@ -44,13 +44,16 @@ MDC_GEMM_TC = 3
 MDC_GEMM_GEMV = 4
 MDC_GEMM_TC_STREAM = 5
 
+MDC_BATCH_BRANCHES = 0
+MDC_BATCH_QUEUE = 1
+
 EXPORTED = (
     "mdc_plan_create", "mdc_plan_destroy", "mdc_plan_info", "mdc_plan_sigma2_max", "mdc_forward",
     "mdc_adjoint", "smdd_step", "mdc_plan_sync_status", "mdc_status_string", "mdc_plan_set_profiling",
     "mdc_plan_stage_times", "mdc_stage_name", "mdc_plan_launch_count", "mdc_forward_static",
     "mdc_plan_get_config", "mdc_plan_set_config", "mdc_plan_autotune", "smdd_step_ex", "smdd_lsqr", "mdc_plan_set_band",
     "mdc_batch_create", "mdc_batch_run", "mdc_batch_info", "mdc_batch_destroy", "mdc_alu_probe",
-    "smdd_step_host", "mdc_plan_set_wait_probe",
+    "smdd_step_host", "mdc_plan_set_wait_probe", "mdc_batch_create_ex",
 )
 
 
@@ -120,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mdc_plan_set_config.argtypes = [vp, ctypes.POINTER(mdc_config)]
     lib.mdc_plan_autotune.argtypes = [vp, i, i, i, ctypes.POINTER(mdc_config), vp]
     lib.mdc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(smdd_member), i, i, vp]
+    lib.mdc_batch_create_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(smdd_member), i, i, i, vp]
     lib.mdc_batch_run.argtypes = [vp, ctypes.c_longlong, i, vp]
     lib.mdc_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
     lib.mdc_batch_destroy.argtypes = [vp]
@@ -396,9 +400,11 @@ class MDCBatch:
     members: list of dicts with keys plan (MDCPlan), X, U_obs, perm (int32 [n_perm][ns]), nb, alpha,
     flags (0 or SMDD_RECIPROCITY), loss (float64 [loss_rows][steps] or None).  The tensors must stay
     alive (and at the same addresses) while the batch lives; this object keeps references to them.
+    mode: MDC_BATCH_BRANCHES (members on n_branches graph branches) or MDC_BATCH_QUEUE (waves of
+    persistent kernels with device work queues; split-BF16 plans with tensor-core products).
     """
 
-    def __init__(self, members: list, n_branches: int = 8, stream=None):
+    def __init__(self, members: list, n_branches: int = 8, stream=None, mode: int = MDC_BATCH_BRANCHES):
         _require_cuda()
         lib = load_library()
         arr = (smdd_member * len(members))()
@@ -432,8 +438,9 @@ class MDCBatch:
             self._keep.append((plan, X, U, perm, loss))
             self.steps.append(steps)
         h = ctypes.c_void_p()
-        _check(lib.mdc_batch_create(ctypes.byref(h), arr, len(members), int(n_branches), _stream_ptr(stream)),
-               "mdc_batch_create")
+        _check(lib.mdc_batch_create_ex(ctypes.byref(h), arr, len(members), int(mode), int(n_branches),
+                                       _stream_ptr(stream)), "mdc_batch_create_ex")
+        self.mode = int(mode)
         self.handle = h.value
         kpe, nbr = ctypes.c_longlong(), ctypes.c_int()
         _check(lib.mdc_batch_info(ctypes.c_void_p(self.handle), ctypes.byref(kpe), ctypes.byref(nbr)), "mdc_batch_info")

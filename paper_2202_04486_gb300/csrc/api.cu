@@ -33,6 +33,10 @@ struct DeviceGuard {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+#ifndef SMDD_TC_ADJ_TMA
+#define SMDD_TC_ADJ_TMA 1   // the split-BF16 adjoint without reciprocity writes its tiles by tensor-map stores
+#endif
+
 }  // namespace
 
 namespace smdd {
@@ -235,7 +239,9 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.nf_active = p->nf_active;
     g.wait_probe = p->wait_probe;
     if (p->gemm_adj == MDC_GEMM_TC)
-        return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_tc_adj(g, recip, p->nf, st); });
+        return launch_stage(p, ST_GEMM_ADJ, st, [&] {
+            return launch_tc_adj(g, recip, p->nf, st, (SMDD_TC_ADJ_TMA && p->xh_map_ok) ? p->xh_map : nullptr);
+        });
     if (p->gemm_adj == MDC_GEMM_GEMV && gemv_supported(p->nv) && !recip && p->nf_active == 0 && nb <= 1024)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] { return launch_gemv_adj(g, p->nf, st); });
     const int tile = p->gemm_adj == MDC_GEMM_SIMT32 ? 32 : p->gemm_adj == MDC_GEMM_SIMT64 ? 64 : 0;
@@ -655,6 +661,80 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
 }
 
 }  // namespace
+
+namespace smdd {
+
+int plan_step_records(mdc_plan_s *p, float *X, const float *U_obs, const int32_t *idx, int nb, float alpha, int flags,
+                      double *loss, StepRecords *r) {
+    if (!p || !X || !U_obs || !idx || !r || nb < 1 || nb > p->nbmax) return MDC_ERR_INVALID_ARG;
+    if (p->prec != MDC_PREC_BF16X3 || (p->gemm_fwd != MDC_GEMM_TC && p->gemm_fwd != MDC_GEMM_TC_STREAM) ||
+        p->gemm_adj != MDC_GEMM_TC || p->nf_active != 0)
+        return MDC_ERR_UNSUPPORTED;
+    const bool recip = flags & SMDD_RECIPROCITY;
+    if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
+    memset(r, 0, sizeof(*r));
+    r->M = p->M;
+    r->variant = p->fft_variant;
+    auto tiles = [&](const TraceGrid &g) {
+        return p->fft_variant == 2 ? fft2_blocks(p->M, g) : fft_blocks(p->M, g);
+    };
+    // model transform
+    r->rfft = base_fft(p);
+    r->rfft.g = model_grid(p, p->nv);
+    r->rfft.tin = X;
+    r->rfft.vec = vec4_ok(p->nt, X);
+    r->rfft.spec = p->Xh;
+    r->rfft_tiles = tiles(r->rfft.g);
+    // forward product (as gemm_forward, on the tile kernel)
+    GemmArgs &g = r->fwd;
+    g.A = p->Xh; g.Dh = p->Dh; g.idx = idx; g.C = p->Uh;
+    g.nv = p->nv; g.nr = p->nr; g.ns = p->ns; g.nb = nb; g.ldr = p->ldr; g.ldb = p->ldb;
+    g.sAf = (long long)p->nv * p->ldr; g.sDf = (long long)p->ns * p->ldr; g.sCf = (long long)p->nv * p->ldb;
+    g.outscale = 1.f;
+    g.status = p->status;
+    g.wait_probe = p->wait_probe;
+    r->fwd_nb = tc_fwd_queue_nb(nb);
+    r->fwd_tiles = tc_fwd_tiles(g, p->nf);
+    // residual step (as step_impl)
+    FftArgs &a = r->resid;
+    a = base_fft(p);
+    a.g = batch_grid(p, nb);
+    a.spec = p->Uh;
+    a.uobs = U_obs;
+    a.idx = idx;
+    a.ns = p->ns;
+    a.gathered = (flags & SMDD_UOBS_GATHERED) ? 1 : 0;
+    a.uo_si = (long long)p->nv * p->nt;
+    a.uo_sj = p->nt;
+    a.vec = vec4_ok(p->nt, U_obs);
+    a.partials = p->partials;
+    a.counter = p->counter;
+    a.loss = loss;
+    r->resid_tiles = tiles(a.g);
+    if (r->resid_tiles <= 0 || r->resid_tiles > p->resid_blocks_max) return MDC_ERR_INVALID_ARG;
+    // adjoint product
+    GemmArgs &h = r->adj;
+    h.A = p->Uh; h.Dh = p->Dh; h.idx = idx; h.C = p->Xh;
+    h.nv = p->nv; h.nr = p->nr; h.ns = p->ns; h.nb = nb; h.ldr = p->ldr; h.ldb = p->ldb;
+    h.sAf = (long long)p->nv * p->ldb; h.sDf = (long long)p->ns * p->ldr; h.sCf = (long long)p->nv * p->ldr;
+    h.outscale = recip ? 0.5f : 1.f;
+    h.status = p->status;
+    h.wait_probe = p->wait_probe;
+    r->adj_tiles = tc_adj_tiles(h, recip, p->nf);
+    r->recip = recip;
+    // update with the spectra of the new model
+    FftArgs &u = r->upd;
+    u = base_fft(p);
+    u.g = model_grid(p, p->nv);
+    u.tout = X;
+    u.vec = vec4_ok(p->nt, X);
+    u.spec = p->Xh;
+    u.alpha = alpha;
+    r->upd_tiles = tiles(u.g);
+    return (r->rfft_tiles < 0 || r->upd_tiles < 0) ? MDC_ERR_INVALID_ARG : MDC_OK;
+}
+
+}  // namespace smdd
 
 extern "C" {
 

@@ -4,7 +4,12 @@
 // permutation, the last slice partial).  The graph holds, in order:
 //   k_epoch_begin  -- for every member, row (e % n_perm) of its permutation table -> its index buffer,
 //                     e read from the batch's device epoch counter;
-//   the steps      -- each member's steps in sequence on one of n_branches parallel branches;
+//   the steps      -- MDC_BATCH_BRANCHES: each member's steps in sequence on one of n_branches parallel
+//                     branches, as the plan's own launches;
+//                     MDC_BATCH_QUEUE: the epoch in waves, wave w holding step w of every member that has
+//                     one; every stage of a wave (model transform in wave 0, forward product, residual
+//                     step, adjoint product, update) is one launch per kernel family of persistent CTAs
+//                     that take (problem, tile) items from a device work queue until it is empty;
 //   k_epoch_end    -- the step losses -> row (e % loss_rows) of each member's loss table, then e += 1.
 // Only device-side state changes between replays, so the same graph serves every epoch.
 #include <algorithm>
@@ -62,11 +67,52 @@ double member_cost(const PlanShape &sh, int nb) {
     return steps * (gemm + fft);
 }
 
+// One launch of the work-queue epoch: stage kind, kernel family, and the queue it drains.
+struct QLaunch {
+    int kind;            // 0 model transform, 1 forward product, 2 residual, 3 adjoint product, 4 update
+    int M, variant;      // trace kernels: FFT length / 2 and variant
+    int key;             // forward: batch block NB; adjoint: reciprocity
+    std::vector<int> members;
+    std::vector<const void *> recs;
+    std::vector<int> tiles;
+    WorkQueue q;
+};
+
+// Group the records of one stage by kernel family into launches (members in order).
+void add_stage(std::vector<QLaunch> &out, int kind, const std::vector<int> &ms, const std::vector<StepRecords> &rec) {
+    std::vector<QLaunch> stage;
+    for (size_t i = 0; i < ms.size(); ++i) {
+        const StepRecords &r = rec[i];
+        int M = 0, var = 0, key = 0, tiles = 0;
+        const void *rp = nullptr;
+        switch (kind) {
+            case 0: M = r.M; var = r.variant; tiles = r.rfft_tiles; rp = &r.rfft; break;
+            case 1: key = r.fwd_nb; tiles = r.fwd_tiles; rp = &r.fwd; break;
+            case 2: M = r.M; var = r.variant; tiles = r.resid_tiles; rp = &r.resid; break;
+            case 3: key = r.recip ? 1 : 0; tiles = r.adj_tiles; rp = &r.adj; break;
+            default: M = r.M; var = r.variant; tiles = r.upd_tiles; rp = &r.upd; break;
+        }
+        if (tiles <= 0) continue;
+        QLaunch *L = nullptr;
+        for (auto &x : stage)
+            if (x.M == M && x.variant == var && x.key == key) L = &x;
+        if (!L) {
+            stage.push_back(QLaunch{kind, M, var, key, {}, {}, {}, WorkQueue{}});
+            L = &stage.back();
+        }
+        L->members.push_back(ms[i]);
+        L->recs.push_back(rp);
+        L->tiles.push_back(tiles);
+    }
+    for (auto &x : stage) out.push_back(std::move(x));
+}
+
 }  // namespace
 
 struct mdc_batch_s {
     int device = 0;
-    int n = 0, n_branches = 0;
+    int n = 0, n_branches = 0, mode = MDC_BATCH_BRANCHES;
+    void *queue_mem = nullptr;       // device: argument records, tile prefix sums, queue counters
     std::vector<smdd_member> members;
     std::vector<int> steps;
     EpochSlot *slots = nullptr;      // device [n]
@@ -90,6 +136,7 @@ int mdc_batch_destroy(mdc_batch_t b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto q : b->cur_idx) cudaFree(q);
     for (auto q : b->cur_loss) cudaFree(q);
+    cudaFree(b->queue_mem);
     cudaFree(b->slots);
     cudaFree(b->epoch);
     if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
@@ -98,7 +145,14 @@ int mdc_batch_destroy(mdc_batch_t b) {
 }
 
 int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_branches, void *stream) {
-    if (!out || !members || n < 1 || n_branches < 1 || n_branches > 64) return MDC_ERR_INVALID_ARG;
+    return mdc_batch_create_ex(out, members, n, MDC_BATCH_BRANCHES, n_branches, stream);
+}
+
+int mdc_batch_create_ex(mdc_batch_t *out, const smdd_member *members, int n, int mode, int n_branches, void *stream) {
+    if (!out || !members || n < 1) return MDC_ERR_INVALID_ARG;
+    if (mode != MDC_BATCH_BRANCHES && mode != MDC_BATCH_QUEUE) return MDC_ERR_INVALID_ARG;
+    if (mode == MDC_BATCH_BRANCHES && (n_branches < 1 || n_branches > 64)) return MDC_ERR_INVALID_ARG;
+    if (mode == MDC_BATCH_QUEUE) n_branches = 1;
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = -1;
@@ -124,6 +178,7 @@ int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_
     if (!b) return MDC_ERR_OOM;
     b->device = dev;
     b->n = n;
+    b->mode = mode;
     b->n_branches = std::min(n_branches, n);
     b->members.assign(members, members + n);
     b->steps.resize(n);
@@ -165,6 +220,81 @@ int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_
         return rc;
     }
 
+    // work-queue epoch: the step records of every wave, grouped into launches, uploaded once
+    std::vector<std::vector<StepRecords>> wave_recs;
+    std::vector<QLaunch> qlaunches;
+    unsigned int *qcounters = nullptr;
+    int n_counters = 0;
+    if (mode == MDC_BATCH_QUEUE) {
+        int maxsteps = 0;
+        for (int m = 0; m < n; ++m) maxsteps = std::max(maxsteps, b->steps[m]);
+        wave_recs.resize(maxsteps);
+        for (int w = 0; rc == MDC_OK && w < maxsteps; ++w) {
+            std::vector<int> ms;
+            for (int m = 0; m < n; ++m)
+                if (b->steps[m] > w) ms.push_back(m);
+            wave_recs[w].resize(ms.size());
+            for (size_t i = 0; rc == MDC_OK && i < ms.size(); ++i) {
+                const int m = ms[i];
+                const smdd_member &mb = members[m];
+                const int nbs = std::min(mb.nb, shapes[m].ns - w * mb.nb);
+                rc = plan_step_records(mb.plan, mb.X, mb.U_obs, b->cur_idx[m] + (long long)w * mb.nb, nbs, mb.alpha,
+                                       mb.flags, b->cur_loss[m] + w, &wave_recs[w][i]);
+            }
+            if (rc != MDC_OK) break;
+            if (w == 0) add_stage(qlaunches, 0, ms, wave_recs[w]);
+            for (int kind = 1; kind <= 4; ++kind) add_stage(qlaunches, kind, ms, wave_recs[w]);
+        }
+        // device layout: FftArgs records | GemmArgs records | tile prefix sums | queue counters
+        size_t nF = 0, nG = 0, nS = 0;
+        for (auto &L : qlaunches) {
+            (L.kind == 1 || L.kind == 3 ? nG : nF) += L.members.size();
+            nS += L.members.size() + 1;
+        }
+        n_counters = (int)qlaunches.size();
+        auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+        const size_t oF = 0, oG = al(oF + nF * sizeof(FftArgs)), oS = al(oG + nG * sizeof(GemmArgs));
+        const size_t oC = al(oS + nS * sizeof(int)), total = al(oC + (size_t)n_counters * sizeof(unsigned int));
+        std::vector<unsigned char> host(total, 0);
+        if (rc == MDC_OK && cudaMalloc(&b->queue_mem, total) != cudaSuccess) {
+            cudaGetLastError();
+            rc = MDC_ERR_OOM;
+        }
+        unsigned char *dev = static_cast<unsigned char *>(b->queue_mem);
+        size_t iF = 0, iG = 0, iS = 0;
+        for (size_t k = 0; rc == MDC_OK && k < qlaunches.size(); ++k) {
+            QLaunch &L = qlaunches[k];
+            const bool gemm = L.kind == 1 || L.kind == 3;
+            const size_t rsz = gemm ? sizeof(GemmArgs) : sizeof(FftArgs);
+            const size_t off = gemm ? oG + iG * rsz : oF + iF * rsz;
+            for (size_t i = 0; i < L.members.size(); ++i) memcpy(&host[off + i * rsz], L.recs[i], rsz);
+            int *st0 = reinterpret_cast<int *>(&host[oS]) + iS;
+            int acc = 0;
+            for (size_t i = 0; i < L.members.size(); ++i) {
+                st0[i] = acc;
+                acc += L.tiles[i];
+            }
+            st0[L.members.size()] = acc;
+            L.q.args = dev + off;
+            L.q.start = reinterpret_cast<const int *>(dev + oS) + iS;
+            L.q.n = (int)L.members.size();
+            L.q.total = acc;
+            L.q.counter = reinterpret_cast<unsigned int *>(dev + oC) + k;
+            (gemm ? iG : iF) += L.members.size();
+            iS += L.members.size() + 1;
+        }
+        if (rc == MDC_OK) {
+            qcounters = reinterpret_cast<unsigned int *>(dev + oC);
+            if (cudaMemcpyAsync(b->queue_mem, host.data(), total, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = MDC_ERR_CUDA;
+        }
+        if (rc != MDC_OK) {
+            mdc_batch_destroy(b);
+            return rc;
+        }
+    }
+
     // branches: members in decreasing cost, each onto the branch with the least work so far
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -201,7 +331,22 @@ int mdc_batch_create(mdc_batch_t *out, const smdd_member *members, int n, int n_
         k_epoch_begin<<<n, 256, 0, cap>>>(b->slots, n, b->epoch);
         if (cudaGetLastError() != cudaSuccess || cudaEventRecord(fork, cap) != cudaSuccess) rc = MDC_ERR_CUDA;
     }
-    for (int k = 0; rc == MDC_OK && k < b->n_branches; ++k) {
+    if (mode == MDC_BATCH_QUEUE && rc == MDC_OK) {
+        if (cudaMemsetAsync(qcounters, 0, (size_t)n_counters * sizeof(unsigned int), cap) != cudaSuccess) rc = MDC_ERR_CUDA;
+        for (size_t k = 0; rc == MDC_OK && k < qlaunches.size(); ++k) {
+            const QLaunch &L = qlaunches[k];
+            cudaError_t e = cudaSuccess;
+            switch (L.kind) {
+                case 0: e = launch_queue_rfft(L.M, L.variant, L.q, cap); break;
+                case 1: e = launch_tc_fwd_queue(L.key, L.q, cap); break;
+                case 2: e = launch_queue_residual(L.M, L.variant, L.q, cap); break;
+                case 3: e = launch_tc_adj_queue(L.key != 0, L.q, cap); break;
+                default: e = launch_queue_update(L.M, L.variant, L.q, cap); break;
+            }
+            if (e != cudaSuccess) rc = MDC_ERR_CUDA;
+        }
+    }
+    for (int k = 0; mode == MDC_BATCH_BRANCHES && rc == MDC_OK && k < b->n_branches; ++k) {
         if (cudaStreamWaitEvent(bs[k], fork, 0) != cudaSuccess) { rc = MDC_ERR_CUDA; break; }
         for (int m : branch[k]) {
             const smdd_member &mb = members[m];

@@ -13,6 +13,7 @@
 #include "smdd_fft2.cuh"
 #include "smdd_fft3.cuh"
 #include "smdd_internal.h"
+#include "work_queue.cuh"
 
 namespace smdd {
 
@@ -55,13 +56,14 @@ struct TileCoord2 {
     bool valid;
 };
 
+// tile bid of the grid (blockIdx.x in a plain launch, the dequeued tile in a work-queue launch)
 template <int M>
-__device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr) {
+__device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr, int bid) {
     constexpr int TR = RegFft<M>::TR;
     const int ti = 1 << g.ti_log2;
     const int tj = TR >> g.ti_log2;
     const int ntile_i = (g.ni + ti - 1) / ti;
-    const int bi = blockIdx.x % ntile_i, bj = blockIdx.x / ntile_i;
+    const int bi = bid % ntile_i, bj = bid / ntile_i;
     TileCoord2 c;
     c.i = bi * ti + (tr & (ti - 1));
     c.j = bj * tj + (tr >> g.ti_log2);
@@ -72,11 +74,11 @@ __device__ __forceinline__ TileCoord2 coord2_of(const TraceGrid &g, int tr) {
 // spectra of the CTA's traces -> shared memory (slot 0 = (Re X[0], Re X[M])); thread binding: trace
 // tr = tid % TR, bins f = tid / TR + it * (THREADS / TR)
 template <int M>
-__device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g) {
+__device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g, int bid) {
     using F = RegFft<M>;
     constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
-    const TileCoord2 c = coord2_of<M>(g, tr);
+    const TileCoord2 c = coord2_of<M>(g, tr, bid);
     float2 v[NIT];
     float nyq = 0.f;
     if (c.valid) {
@@ -97,11 +99,11 @@ __device__ __forceinline__ void tile2_load(float2 *sm, const float2 *__restrict_
 }
 
 template <int M>
-__device__ __forceinline__ void tile2_store(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g) {
+__device__ __forceinline__ void tile2_store(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g, int bid) {
     using F = RegFft<M>;
     constexpr int TR = F::TR, STR = F::STRIDE, STEP = F::THREADS / TR, NIT = M / STEP;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
-    const TileCoord2 c = coord2_of<M>(g, tr);
+    const TileCoord2 c = coord2_of<M>(g, tr, bid);
     if (!c.valid) return;
     const float2 *b = sm + tr * STR;
     float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
@@ -134,12 +136,12 @@ __device__ __forceinline__ void store_z(float *y, int n, int nt, bool vec, float
 }
 
 template <int M>
-__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_rfft(FftArgs a) {
+__device__ __forceinline__ void rfft2_body(const FftArgs &a, int bid) {
     extern __shared__ __align__(16) float2 sm[];
     using F = RegFft<M>;
     constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    const TileCoord2 c = coord2_of<M>(a.g, tr, bid);
     float2 *buf = sm + tr * F::STRIDE;
     const float *x = a.tin + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     float2 v[P];
@@ -147,18 +149,24 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_rfft(FftArgs a) {
     for (int m = 0; m < P; ++m) v[m] = (m < P / 2 && c.valid) ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
     F::fwd(v, buf, t, a.tw, a.twN);
     __syncthreads();
-    tile2_store<M>(sm, a.spec, a.g);
+    tile2_store<M>(sm, a.spec, a.g, bid);
+}
+
+template <int M>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_rfft(FftArgs a) {
+    rfft2_body<M>(a, blockIdx.x);
 }
 
 template <int M>
 __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_irfft_out(FftArgs a) {
+    const int bid = blockIdx.x;
     extern __shared__ __align__(16) float2 sm[];
     using F = RegFft<M>;
     constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    tile2_load<M>(sm, a.spec, a.g);
+    tile2_load<M>(sm, a.spec, a.g, bid);
     __syncthreads();
-    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    const TileCoord2 c = coord2_of<M>(a.g, tr, bid);
     float2 *buf = sm + tr * F::STRIDE;
     float2 v[P];
     F::inv(v, buf, t, a.tw, a.twN);
@@ -183,14 +191,14 @@ __device__ __forceinline__ double block_sum2(double v, double *red) {
 
 // residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], FP64 loss partials, Rh = rfft(R) in place
 template <int M>
-__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) {
+__device__ __forceinline__ void residual2_body(const FftArgs &a, int bid, int nblk) {
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[32];
     __shared__ bool am_last;
     using F = RegFft<M>;
     constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    const TileCoord2 c = coord2_of<M>(a.g, tr, bid);
     const float *uo = nullptr;
     if (c.valid) {
         int row = c.i;
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) 
 #pragma unroll
         for (int m = 0; m < P / 2; ++m) o[m] = uo ? load_z(uo, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
     }
-    tile2_load<M>(sm, a.spec, a.g);
+    tile2_load<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * F::STRIDE;
     float2 v[P];
@@ -235,12 +243,11 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) 
     }
     F::fwd(v, buf, t, a.tw, a.twN);
     __syncthreads();
-    tile2_store<M>(sm, a.spec, a.g);
+    tile2_store<M>(sm, a.spec, a.g, bid);
 
     const double bs = block_sum2(l2, red);
     if (threadIdx.x == 0) {
-        const int nblk = gridDim.x;
-        a.partials[blockIdx.x] = bs;
+        a.partials[bid] = bs;
         __threadfence();
         const unsigned prev = atomicAdd(a.counter, 1u);
         am_last = (prev == (unsigned)(nblk - 1));
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) 
     if (am_last) {   // block-uniform
         __threadfence();
         double s = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&a.partials[b]);
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(&a.partials[b]);
         s = block_sum2(s, red);   // fixed assignment and order: deterministic
         if (threadIdx.x == 0) {
             if (a.loss) *a.loss = 0.5 * s;
@@ -258,21 +265,26 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) 
     }
 }
 
+template <int M>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual(FftArgs a) {
+    residual2_body<M>(a, blockIdx.x, gridDim.x);
+}
+
 // update step: g = s * irfft(Gh)[0:nt]; X <- X - alpha g; optionally Gh <- rfft(X_new) in place
 template <int M, bool KEEP>
-__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_update(FftArgs a) {
+__device__ __forceinline__ void update2_body(const FftArgs &a, int bid) {
     extern __shared__ __align__(16) float2 sm[];
     using F = RegFft<M>;
     constexpr int T = F::T, P = F::P;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord2 c = coord2_of<M>(a.g, tr);
+    const TileCoord2 c = coord2_of<M>(a.g, tr, bid);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     float2 xo[P / 2];
     if constexpr (F::PREFETCH) {
 #pragma unroll
         for (int m = 0; m < P / 2; ++m) xo[m] = c.valid ? load_z(x, t + T * m, a.nt, a.vec) : make_float2(0.f, 0.f);
     }
-    tile2_load<M>(sm, a.spec, a.g);
+    tile2_load<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * F::STRIDE;
     float2 v[P];
@@ -298,7 +310,49 @@ __global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_update(FftArgs a) {
     if constexpr (KEEP) {
         F::fwd(v, buf, t, a.tw, a.twN);
         __syncthreads();
-        tile2_store<M>(sm, a.spec, a.g);
+        tile2_store<M>(sm, a.spec, a.g, bid);
+    }
+}
+
+template <int M, bool KEEP>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_update(FftArgs a) {
+    update2_body<M, KEEP>(a, blockIdx.x);
+}
+
+// work-queue forms: persistent CTAs taking (problem, tile) items until the queue is empty
+template <int M>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_rfft_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        rfft2_body<M>(sa, tile);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_residual_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        residual2_body<M>(sa, tile, __ldg(q.start + m + 1) - __ldg(q.start + m));
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(RegFft<M>::THREADS, 2) k2_update_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        update2_body<M, true>(sa, tile);
     }
 }
 
@@ -378,6 +432,9 @@ static cudaError_t prepare2_m() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_residual<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_update<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_update<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_rfft_q<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_residual_q<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2_update_q<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return e;
 }
 
@@ -424,6 +481,28 @@ cudaError_t launch2_update(int M, bool keep, const FftArgs &a, cudaStream_t st) 
         else k2_update<MM, false><<<nb, RegFft<MM>::THREADS, RegFft<MM>::SMEM, st>>>(a);
     });
     return cudaGetLastError();
+}
+
+template <class KF>
+static cudaError_t launch2_queue_kernel(KF kern, int threads, size_t smem, const WorkQueue &q, cudaStream_t st) {
+    if (q.total <= 0) return cudaSuccess;
+    kern<<<queue_grid(kern, threads, smem, q.total), threads, smem, st>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch2_queue_rfft(int M, const WorkQueue &q, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, { return launch2_queue_kernel(k2_rfft_q<MM>, RegFft<MM>::THREADS, RegFft<MM>::SMEM, q, st); });
+    return cudaSuccess;
+}
+
+cudaError_t launch2_queue_residual(int M, const WorkQueue &q, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, { return launch2_queue_kernel(k2_residual_q<MM>, RegFft<MM>::THREADS, RegFft<MM>::SMEM, q, st); });
+    return cudaSuccess;
+}
+
+cudaError_t launch2_queue_update(int M, const WorkQueue &q, cudaStream_t st) {
+    SMDD_SWITCH_M2(M, { return launch2_queue_kernel(k2_update_q<MM>, RegFft<MM>::THREADS, RegFft<MM>::SMEM, q, st); });
+    return cudaSuccess;
 }
 
 }  // namespace smdd

@@ -20,6 +20,7 @@
 
 #include "smdd_fft.cuh"
 #include "smdd_internal.h"
+#include "work_queue.cuh"
 
 namespace smdd {
 
@@ -28,13 +29,14 @@ struct TileCoord {
     bool valid;
 };
 
+// tile bid of the grid (blockIdx.x in a plain launch, the dequeued tile in a work-queue launch)
 template <int M>
-__device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr) {
+__device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr, int bid) {
     constexpr int TR = Team<M>::TR;
     const int ti = 1 << g.ti_log2;
     const int tj = TR >> g.ti_log2;
     const int ntile_i = (g.ni + ti - 1) / ti;
-    const int bi = blockIdx.x % ntile_i, bj = blockIdx.x / ntile_i;
+    const int bi = bid % ntile_i, bj = bid / ntile_i;
     TileCoord c;
     c.i = bi * ti + (tr & (ti - 1));
     c.j = bj * tj + (tr >> g.ti_log2);
@@ -42,13 +44,95 @@ __device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr) {
     return c;
 }
 
+#ifndef SMDD_FFT_PAIR_IO
+#define SMDD_FFT_PAIR_IO 1   // spectrum tiles moved as 16-byte pairs of adjacent traces where the grid allows
+#endif
+
+// The CTA's traces come in pairs adjacent along the contiguous spectrum axis (2 or more consecutive i,
+// an even TR): a thread then moves the bins of two traces with one 16-byte access.
+template <int M>
+__device__ __forceinline__ bool pair_io(const TraceGrid &g) {
+    return SMDD_FFT_PAIR_IO && Team<M>::TR % 2 == 0 && g.ti_log2 >= 1 && g.ssi == 1 && (g.ssj % 2) == 0 &&
+           (g.ssf % 2) == 0;
+}
+
+// Spectra of the CTA's traces -> shared memory, paired form: traces 2p, 2p+1 (p = tid % (TR/2)), bins
+// f = tid / (TR/2) + it * 2T (it < P/2), plus f = M for tid < TR/2.
+template <int M>
+__device__ __forceinline__ void tile_load_spec_pair(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g, int bid) {
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T, H = TR / 2;
+    const int pr = threadIdx.x % H, f0 = threadIdx.x / H;
+    const TileCoord c0 = coord_of<M>(g, 2 * pr, bid), c1 = coord_of<M>(g, 2 * pr + 1, bid);
+    float4 v[P / 2];
+    float2 nyq = make_float2(0.f, 0.f);
+    if (c0.valid) {
+        // c0.i is even and the strides are even: 16-byte aligned; the second trace (c1.i = c0.i + 1) may lie
+        // past ni, where the pair reads the padding column of the spectra (ldr is even) and drops it
+        const float2 *s = spec + (long long)c0.i * g.ssi + (long long)c0.j * g.ssj;
+#pragma unroll
+        for (int it = 0; it < P / 2; ++it) v[it] = __ldcs(reinterpret_cast<const float4 *>(s + (long long)(f0 + it * 2 * T) * g.ssf));
+        if (f0 == 0) {
+            const float4 w = __ldcs(reinterpret_cast<const float4 *>(s + (long long)M * g.ssf));
+            nyq = make_float2(w.x, w.z);
+        }
+    } else {
+#pragma unroll
+        for (int it = 0; it < P / 2; ++it) v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool ok1 = c1.valid;
+    float2 *b0 = sm + (2 * pr) * STR, *b1 = b0 + STR;
+#pragma unroll
+    for (int it = 0; it < P / 2; ++it) {
+        const int f = f0 + it * 2 * T;
+        const float2 x0 = make_float2(v[it].x, v[it].y), x1 = ok1 ? make_float2(v[it].z, v[it].w) : make_float2(0.f, 0.f);
+        if (f == 0) {
+            b0[0] = make_float2(x0.x, nyq.x);
+            b1[0] = make_float2(x1.x, ok1 ? nyq.y : 0.f);
+        } else {
+            b0[padi(f)] = x0;
+            b1[padi(f)] = x1;
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void tile_store_spec_pair(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g, int bid) {
+    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T, H = TR / 2;
+    const int pr = threadIdx.x % H, f0 = threadIdx.x / H;
+    const TileCoord c0 = coord_of<M>(g, 2 * pr, bid), c1 = coord_of<M>(g, 2 * pr + 1, bid);
+    if (!c0.valid) return;
+    const float2 *b0 = sm + (2 * pr) * STR, *b1 = b0 + STR;
+    float2 *s = spec + (long long)c0.i * g.ssi + (long long)c0.j * g.ssj;
+    if (c1.valid) {
+#pragma unroll
+        for (int it = 0; it < P / 2; ++it) {
+            const int f = f0 + it * 2 * T;
+            const float2 x0 = (f == 0) ? make_float2(b0[0].x, 0.f) : b0[padi(f)];
+            const float2 x1 = (f == 0) ? make_float2(b1[0].x, 0.f) : b1[padi(f)];
+            *reinterpret_cast<float4 *>(s + (long long)f * g.ssf) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+        if (f0 == 0) *reinterpret_cast<float4 *>(s + (long long)M * g.ssf) = make_float4(b0[0].y, 0.f, b1[0].y, 0.f);
+    } else {   // the second trace lies past ni: its slot of the spectra is left untouched
+#pragma unroll
+        for (int it = 0; it < P / 2; ++it) {
+            const int f = f0 + it * 2 * T;
+            s[(long long)f * g.ssf] = (f == 0) ? make_float2(b0[0].x, 0.f) : b0[padi(f)];
+        }
+        if (f0 == 0) s[(long long)M * g.ssf] = make_float2(b0[0].y, 0.f);
+    }
+}
+
 // Spectra of the CTA's traces -> shared memory.  Slot 0 of each trace holds (Re X[0], Re X[M]).
 // Thread binding: trace tr = tid % TR, bins f = tid / TR + it * T (it < P), plus f = M for tid < TR.
 template <int M>
-__device__ __forceinline__ void tile_load_spec(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g) {
+__device__ __forceinline__ void tile_load_spec(float2 *sm, const float2 *__restrict__ spec, const TraceGrid &g, int bid) {
+    if (pair_io<M>(g)) {
+        tile_load_spec_pair<M>(sm, spec, g, bid);
+        return;
+    }
     constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
-    const TileCoord c = coord_of<M>(g, tr);
+    const TileCoord c = coord_of<M>(g, tr, bid);
     float2 v[P];
     float nyq = 0.f;
     if (c.valid) {
@@ -70,10 +154,14 @@ __device__ __forceinline__ void tile_load_spec(float2 *sm, const float2 *__restr
 }
 
 template <int M>
-__device__ __forceinline__ void tile_store_spec(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g) {
+__device__ __forceinline__ void tile_store_spec(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g, int bid) {
+    if (pair_io<M>(g)) {
+        tile_store_spec_pair<M>(sm, spec, g, bid);
+        return;
+    }
     constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
     const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
-    const TileCoord c = coord_of<M>(g, tr);
+    const TileCoord c = coord_of<M>(g, tr, bid);
     if (!c.valid) return;
     const float2 *b = sm + tr * STR;
     float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
@@ -159,11 +247,11 @@ __device__ __forceinline__ void store_quad(float *y, int i0, int nt, bool vec, f
 // kernels
 // ------------------------------------------------------------------------------------------------
 template <int M, int V>
-__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArgs a) {
+__device__ __forceinline__ void rfft_body(const FftArgs &a, int bid) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord c = coord_of<M>(a.g, tr);
+    const TileCoord c = coord_of<M>(a.g, tr, bid);
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float4 h[NPAIR];
     float2 v[FFT_P];
@@ -172,18 +260,24 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArg
     pairs_to_regs<M, V>(h, v);
     rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
     __syncthreads();
-    tile_store_spec<M>(sm, a.spec, a.g);
+    tile_store_spec<M>(sm, a.spec, a.g, bid);
+}
+
+template <int M, int V>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft(FftArgs a) {
+    rfft_body<M, V>(a, blockIdx.x);
 }
 
 // spectra -> s * irfft, causal window [0, nt)
 template <int M, int V>
 __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_irfft_out(FftArgs a) {
+    const int bid = blockIdx.x;
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    tile_load_spec<M>(sm, a.spec, a.g);
+    tile_load_spec<M>(sm, a.spec, a.g, bid);
     __syncthreads();
-    const TileCoord c = coord_of<M>(a.g, tr);
+    const TileCoord c = coord_of<M>(a.g, tr, bid);
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
     irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
@@ -224,14 +318,15 @@ __device__ __forceinline__ float4 resid_quad(float2 p0, float2 p1, float4 o, flo
 
 // Residual step: R = s * irfft(Uh)[0:nt] - U_obs[row], loss partial 1/2 sum R^2 (FP64), Rh = rfft(R)
 // written in place over Uh.  Trace grid: i = batch entry b, j = virtual source v.
+// tile bid of nblk tiles; the last tile to finish (atomic ticket) sums the partials of all nblk
 template <int M, int V>
-__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(FftArgs a) {
+__device__ __forceinline__ void residual_body(const FftArgs &a, int bid, int nblk) {
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[32];
     __shared__ bool am_last;
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord c = coord_of<M>(a.g, tr);
+    const TileCoord c = coord_of<M>(a.g, tr, bid);
 
     // observed row for this trace, prefetched before the transforms
     const float *uo = nullptr;
@@ -249,7 +344,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     float4 o[NPAIR];
     load_pairs<M, V>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o);
 
-    tile_load_spec<M>(sm, a.spec, a.g);
+    tile_load_spec<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
@@ -274,13 +369,12 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     team_sync<T>();          // every thread of the team has finished reading buf
     rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
     __syncthreads();
-    tile_store_spec<M>(sm, a.spec, a.g);
+    tile_store_spec<M>(sm, a.spec, a.g, bid);
 
     // deterministic loss: per-block partials, summed in block order by the last block to finish
     const double bs = block_sum(l2, red);
     if (threadIdx.x == 0) {
-        const int nblk = gridDim.x;
-        a.partials[blockIdx.x] = bs;
+        a.partials[bid] = bs;
         __threadfence();
         const unsigned prev = atomicAdd(a.counter, 1u);
         am_last = (prev == (unsigned)(nblk - 1));
@@ -289,7 +383,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     if (am_last) {   // block-uniform
         __threadfence();
         double s = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&a.partials[b]);
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(&a.partials[b]);
         s = block_sum(s, red);   // fixed assignment and order: deterministic
         if (threadIdx.x == 0) {
             if (a.loss) *a.loss = 0.5 * s;
@@ -298,20 +392,25 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
     }
 }
 
+template <int M, int V>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(FftArgs a) {
+    residual_body<M, V>(a, blockIdx.x, gridDim.x);
+}
+
 // Update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g (SGD), or with the causality mute and/or Nesterov
 // momentum (see the else branch);  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
 template <int M, int V, bool KEEP, bool EXT>
-__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftArgs a) {
+__device__ __forceinline__ void update_body(const FftArgs &a, int bid) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const TileCoord c = coord_of<M>(a.g, tr);
+    const TileCoord c = coord_of<M>(a.g, tr, bid);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     float4 xo[NPAIR];
     load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo);      // model samples, prefetched
 
-    tile_load_spec<M>(sm, a.spec, a.g);
+    tile_load_spec<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
@@ -392,7 +491,49 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftA
         team_sync<T>();
         rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
         __syncthreads();
-        tile_store_spec<M>(sm, a.spec, a.g);
+        tile_store_spec<M>(sm, a.spec, a.g, bid);
+    }
+}
+
+template <int M, int V, bool KEEP, bool EXT>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update(FftArgs a) {
+    update_body<M, V, KEEP, EXT>(a, blockIdx.x);
+}
+
+// work-queue forms: persistent CTAs taking (problem, tile) items until the queue is empty
+template <int M, int V>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_rfft_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        rfft_body<M, V>(sa, tile);
+    }
+}
+
+template <int M, int V>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        residual_body<M, V>(sa, tile, __ldg(q.start + m + 1) - __ldg(q.start + m));
+    }
+}
+
+template <int M, int V>
+__global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_q(WorkQueue q) {
+    const FftArgs *args = static_cast<const FftArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ FftArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        update_body<M, V, true, false>(sa, tile);
     }
 }
 
@@ -621,6 +762,9 @@ static cudaError_t prepare_m() {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residual<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rfft_q<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residual_q<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_q<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         });
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -726,6 +870,48 @@ cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
         }
     });
     return cudaGetLastError();
+}
+
+// work-queue launches (variant 2 goes to the register-FFT kernels)
+template <class KF>
+static cudaError_t launch_queue_kernel(KF kern, int M_threads, size_t smem, const WorkQueue &q, cudaStream_t st) {
+    if (q.total <= 0) return cudaSuccess;
+    const int grid = queue_grid(kern, M_threads, smem, q.total);
+    kern<<<grid, M_threads, smem, st>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_queue_rfft(int M, int variant, const WorkQueue &q, cudaStream_t st) {
+    if (variant == 2) return launch2_queue_rfft(M, q, st);
+    cudaError_t e = cudaSuccess;
+    SMDD_SWITCH_M(M, {
+        with_variant<MM>(variant, [&](auto vc) {
+            e = launch_queue_kernel(k_rfft_q<MM, decltype(vc)::value>, Team<MM>::THREADS, Team<MM>::SMEM, q, st);
+        });
+    });
+    return e;
+}
+
+cudaError_t launch_queue_residual(int M, int variant, const WorkQueue &q, cudaStream_t st) {
+    if (variant == 2) return launch2_queue_residual(M, q, st);
+    cudaError_t e = cudaSuccess;
+    SMDD_SWITCH_M(M, {
+        with_variant<MM>(variant, [&](auto vc) {
+            e = launch_queue_kernel(k_residual_q<MM, decltype(vc)::value>, Team<MM>::THREADS, Team<MM>::SMEM, q, st);
+        });
+    });
+    return e;
+}
+
+cudaError_t launch_queue_update(int M, int variant, const WorkQueue &q, cudaStream_t st) {
+    if (variant == 2) return launch2_queue_update(M, q, st);
+    cudaError_t e = cudaSuccess;
+    SMDD_SWITCH_M(M, {
+        with_variant<MM>(variant, [&](auto vc) {
+            e = launch_queue_kernel(k_update_q<MM, decltype(vc)::value>, Team<MM>::THREADS, Team<MM>::SMEM, q, st);
+        });
+    });
+    return e;
 }
 
 }  // namespace smdd

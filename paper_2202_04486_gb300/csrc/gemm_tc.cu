@@ -21,6 +21,7 @@
 #include "smdd_fft.cuh"
 #include "smdd_internal.h"
 #include "tc_common.cuh"
+#include "work_queue.cuh"
 
 namespace smdd {
 
@@ -89,8 +90,11 @@ struct TcFwd {
     static constexpr uint32_t TMEM_COLS = 2 * NB <= 32 ? 32 : 2 * NB;   // power of two >= 32
 };
 
-template <int NB, int NSTAGE>
-__global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(GemmArgs a) {
+// Tile (bx, by, bz) = (row block of 128 virtual sources, batch block of NB, bin f).  Q: a work-queue
+// item of a persistent CTA, which owns its TMEM (tmem_q) for all its items; the barriers are
+// invalidated at the end of the item so that the next one can initialise them again.
+template <int NB, int NSTAGE, bool Q>
+__device__ __forceinline__ void tc_fwd_body(const GemmArgs &a, int bx, int by, int bz, uint32_t tmem_q) {
     using G = TcFwd<NB, NSTAGE>;
     extern __shared__ uint8_t tc_raw[];
     __shared__ uint64_t bars[2];
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     __shared__ int drows[NB];
     __shared__ int fail, issued;
     uint8_t *sm = align1024(tc_raw);
-    const int f = blockIdx.z, v0 = blockIdx.x * 128, b0 = blockIdx.y * NB;
+    const int f = bz, v0 = bx * 128, b0 = by * NB;
     if (a.nf_active > 0 && f >= a.nf_active) {   // above the band limit: zero products, no TMEM
         zero_tile(a.C + (long long)f * a.sCf, a.ldb, v0, 128, b0, NB, a.nv, a.nb);
         return;
@@ -125,11 +129,11 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
         issued = 0;
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
+    if (!Q && warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_holder;
+    const uint32_t tmem = Q ? tmem_q : tmem_holder;
     constexpr uint32_t idp = umma_idesc(128, NB, 0, 0, 0), idn = umma_idesc(128, NB, 0, 0, 1);
     // failure-path check: before any copy or product, wait on a barrier that nothing arrives on (phase
     // 0 of bars[1] never completes here) for a short limit, then take the timeout path below
@@ -219,6 +223,47 @@ __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(Gemm
     } else if (tid == 0) {
         atomicOr(a.status, 2);
     }
+    if constexpr (Q) {
+        __syncthreads();   // every wait on the barriers of this item is over
+        if (tid == 0) {
+            mbar_inval(&bars[0]);
+            mbar_inval(&bars[1]);
+        }
+    } else {
+        if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+    }
+}
+
+template <int NB, int NSTAGE>
+__global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(GemmArgs a) {
+    tc_fwd_body<NB, NSTAGE, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, 0);
+}
+
+// work-queue form: persistent CTAs (TMEM allocated once) taking (problem, tile) items; tile t of a
+// problem is (bx, by, bz) with t = (bz gy + by) gx + bx, gx = ceil(nv / 128), gy = ceil(nb / NB)
+template <int NB>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_fwd_q(WorkQueue q) {
+    using G = TcFwd<NB, 1>;
+    __shared__ uint32_t holder;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tmem_alloc(&holder, G::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = holder;
+    const GemmArgs *args = static_cast<const GemmArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ GemmArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        const GemmArgs &a = sa;
+        const int gx = (a.nv + 127) / 128, gy = (a.nb + NB - 1) / NB;
+        const int bx = tile % gx, r = tile / gx;
+        tc_fwd_body<NB, 1, true>(a, bx, r % gy, r / gy, tmem);
+    }
+    tc_fence_before();
+    __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
 }
 
@@ -254,8 +299,10 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <bool RECIP>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
+// Tile bx of bin by (the upper-triangular enumeration with reciprocity); Q as for tc_fwd_body.
+template <bool RECIP, bool Q, bool TMA = false>
+__device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, uint32_t tmem_q,
+                                            const CUtensorMap *tmap = nullptr) {
     using G = TcAdj;
     constexpr int KC = G::KC;
     extern __shared__ uint8_t tc_raw[];
@@ -266,16 +313,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
     uint8_t *sm = align1024(tc_raw);
     uint8_t *sA = sm, *sB = sm + 4 * G::PLANE;
     float2 *stg = reinterpret_cast<float2 *>(sm + G::OPER);
-    const int f = blockIdx.y;
+    const int f = by;
     int vb, rb;
     if (RECIP) {
-        int t = blockIdx.x, row = 0, len = a.tiles_v;
+        int t = bx, row = 0, len = a.tiles_v;
         while (t >= len) { t -= len; ++row; --len; }
         vb = row;
         rb = row + t;
     } else {
-        vb = blockIdx.x / a.tiles_r;
-        rb = blockIdx.x % a.tiles_r;
+        vb = bx / a.tiles_r;
+        rb = bx % a.tiles_r;
     }
     const int v0 = vb * 128, r0 = rb * 128;
     if (a.nf_active > 0 && f >= a.nf_active) {   // above the band limit: zero products, no TMEM
@@ -302,11 +349,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
         issued = 0;
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
+    if (!Q && warp == 0) tmem_alloc(&tmem_holder, G::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_holder;
+    const uint32_t tmem = Q ? tmem_q : tmem_holder;
     constexpr uint32_t idp = umma_idesc(128, 128, 1, 1, 0), idn = umma_idesc(128, 128, 1, 1, 1);
     // failure-path check: before any copy or product, wait on a barrier that nothing arrives on for a
     // short limit, then take the timeout path below
@@ -392,6 +439,54 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
     // after a timeout, give products still in flight one more bounded wait before TMEM is freed
     if (!ok && issued) mbar_wait_bounded(&bar, phase & 1);
     tc_fence_after();
+    if constexpr (!RECIP && TMA) {
+        // epilogue by the tensor memory accelerator, in two passes of 64 columns: TMEM -> four staged
+        // boxes of 16 complex x 128 rows (128-byte swizzle: granule g of row m at g ^ (m % 8)) -> four tiled
+        // stores of the tensor map of C (clipped at nv and nr)
+        for (int pass = 0; pass < 2; ++pass) {
+            if (ok) {
+                const int q = warp & 3, hc = warp >> 2;   // lanes 32q.., columns 32hc.. of this pass
+                const int row = 32 * q + lane;
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    const int col = 64 * pass + 32 * hc + c0;
+                    float re[16], im[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + col, re);
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128 + col, im);
+                    uint8_t *box = sm + ((32 * hc + c0) >> 4) * (128 * 128) + row * 128;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g)
+                        *reinterpret_cast<float4 *>(box + ((g ^ (row & 7)) << 4)) =
+                            make_float4(re[2 * g] * a.outscale, im[2 * g] * a.outscale, re[2 * g + 1] * a.outscale,
+                                        im[2 * g + 1] * a.outscale);
+                }
+            }
+            fence_async_smem();   // the staged boxes are visible to the tensor memory accelerator
+            tc_fence_before();
+            __syncthreads();
+            if (ok && tid == 0) {
+#pragma unroll
+                for (int b4 = 0; b4 < 4; ++b4) {
+                    const int r = r0 + 64 * pass + 16 * b4;
+                    if (r < a.nr) tma_store_3d(tmap, sm + b4 * (128 * 128), 2 * r, v0, f);
+                }
+                bulk_commit();
+                bulk_wait_read();   // the staging may be written again
+            }
+            __syncthreads();
+        }
+        if (ok && tid == 0) bulk_wait_all();
+        if (!ok && tid == 0) atomicOr(a.status, 2);
+        if constexpr (Q) {
+            if (tid == 0) {
+                mbar_inval(&bar);
+                mbar_inval(&probe_bar);
+            }
+        } else {
+            if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+        }
+        return;
+    }
     // epilogue in two passes of 64 columns: TMEM -> shared staging [128][65] -> coalesced rows (and
     // the mirror)
     float2 *out = reinterpret_cast<float2 *>(sm);
@@ -430,7 +525,52 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
         __syncthreads();
     }
     if (!ok && tid == 0) atomicOr(a.status, 2);
-    if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+    if constexpr (Q) {
+        // the last loop iteration ended with a barrier after every wait: the barriers are free
+        if (tid == 0) {
+            mbar_inval(&bar);
+            mbar_inval(&probe_bar);
+        }
+    } else {
+        if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
+    }
+}
+
+template <bool RECIP>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
+    tc_adj_body<RECIP, false>(a, blockIdx.x, blockIdx.y, 0);
+}
+
+// the adjoint without reciprocity with its tile written by the tensor memory accelerator (tmap: the
+// tensor map of the gradient spectra, i.e. of the model-spectra buffer, FP32 [nf][nv][2 nr])
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj_tma(GemmArgs a, const __grid_constant__ CUtensorMap tmap) {
+    tc_adj_body<false, false, true>(a, blockIdx.x, blockIdx.y, 0, &tmap);
+}
+
+// work-queue form: tile t of a problem is (bx, by) = (t % tiles, t / tiles) with tiles the output tiles
+// of one bin (the upper triangle with reciprocity); tiles_v / tiles_r are set in the argument records
+template <bool RECIP>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj_q(WorkQueue q) {
+    __shared__ uint32_t holder;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tmem_alloc(&holder, TcAdj::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = holder;
+    const GemmArgs *args = static_cast<const GemmArgs *>(q.args);
+    int m = 0, tile = 0;
+    __shared__ GemmArgs sa;
+    while (queue_next(q, m, tile) >= 0) {
+        queue_args(args + m, sa);
+        __syncthreads();
+        const GemmArgs &a = sa;
+        const int tiles = RECIP ? a.tiles_v * (a.tiles_v + 1) / 2 : a.tiles_v * a.tiles_r;
+        tc_adj_body<RECIP, true>(a, tile % tiles, tile / tiles, tmem);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TcAdj::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -668,6 +808,12 @@ cudaError_t tc_prepare() {
     if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<64>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_q<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, 1>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_q<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, 1>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd_q<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, 1>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     return cudaSuccess;
 }
 
@@ -721,12 +867,47 @@ cudaError_t launch_tc_fwd_stream(const GemmArgs &a, const void *map, int nf, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t st) {
+int tc_fwd_queue_nb(int nb) { return nb <= 16 ? 16 : nb <= 32 ? 32 : 64; }
+
+int tc_fwd_tiles(const GemmArgs &a, int nf) {
+    const int NB = tc_fwd_queue_nb(a.nb);
+    return ((a.nv + 127) / 128) * ((a.nb + NB - 1) / NB) * nf;
+}
+
+int tc_adj_tiles(GemmArgs &a, bool recip, int nf) {
+    a.tiles_v = (a.nv + 127) / 128;
+    a.tiles_r = (a.nr + 127) / 128;
+    return (recip ? a.tiles_v * (a.tiles_v + 1) / 2 : a.tiles_v * a.tiles_r) * nf;
+}
+
+cudaError_t launch_tc_fwd_queue(int NB, const WorkQueue &q, cudaStream_t st) {
+    if (q.total <= 0) return cudaSuccess;
+    if (NB == 16) k_tc_fwd_q<16><<<queue_grid(k_tc_fwd_q<16>, TC_THREADS, TcFwd<16, 1>::SMEM, q.total), TC_THREADS, TcFwd<16, 1>::SMEM, st>>>(q);
+    else if (NB == 32) k_tc_fwd_q<32><<<queue_grid(k_tc_fwd_q<32>, TC_THREADS, TcFwd<32, 1>::SMEM, q.total), TC_THREADS, TcFwd<32, 1>::SMEM, st>>>(q);
+    else k_tc_fwd_q<64><<<queue_grid(k_tc_fwd_q<64>, TC_THREADS, TcFwd<64, 1>::SMEM, q.total), TC_THREADS, TcFwd<64, 1>::SMEM, st>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_adj_queue(bool recip, const WorkQueue &q, cudaStream_t st) {
+    if (q.total <= 0) return cudaSuccess;
+    if (recip) k_tc_adj_q<true><<<queue_grid(k_tc_adj_q<true>, TC_THREADS, TcAdj::SMEM, q.total), TC_THREADS, TcAdj::SMEM, st>>>(q);
+    else k_tc_adj_q<false><<<queue_grid(k_tc_adj_q<false>, TC_THREADS, TcAdj::SMEM, q.total), TC_THREADS, TcAdj::SMEM, st>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t st, const void *map) {
     GemmArgs a = a0;
     a.tiles_v = (a.nv + 127) / 128;
     a.tiles_r = (a.nr + 127) / 128;
-    if (recip) k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
-    else k_tc_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+    if (recip) {
+        k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+    } else if (map) {
+        CUtensorMap tmap;
+        memcpy(&tmap, map, sizeof(tmap));
+        k_tc_adj_tma<<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
+    } else {
+        k_tc_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -80,6 +80,17 @@ __device__ __forceinline__ void zero_tile(float2 *C, long long ld, int r0, int n
     }
 }
 
+// A device work queue over the tiles of one kernel's launches for several problems (the work-queue
+// epochs of the many-problem runner): item w < total belongs to member m with start[m] <= w < start[m+1]
+// and is tile w - start[m] of that member's launch.  The persistent queue kernels take items in order by
+// an atomic add on *counter, which must be zero before the launch.
+struct WorkQueue {
+    const void *args;        // device array of n argument records (FftArgs or GemmArgs)
+    const int *start;        // device [n + 1]: exclusive prefix sums of the members' tile counts
+    int n, total;
+    unsigned int *counter;
+};
+
 // FFT lengths of the trace kernels: powers of two 64 .. 8192 and 3072 (api.cu)
 bool nfft_supported(int nfft);
 int default_nfft(int nt);   // the shortest supported length >= max(2 nt - 1, 64)
@@ -109,6 +120,16 @@ cudaError_t launch2_irfft_out(int M, const FftArgs &a, cudaStream_t st);
 cudaError_t launch2_residual(int M, const FftArgs &a, int nblocks_expected, cudaStream_t st);
 cudaError_t launch2_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
 
+// work-queue forms of the trace kernels (rfft, residual step, SGD update with the new model's spectra),
+// for FFT variant 0, 1 (radix orders) or 2 (register FFT): CTAs resident on every SM, each taking tiles
+// from the queue until it is empty.  Tile counts per member: fft_blocks / fft2_blocks of its grid.
+cudaError_t launch_queue_rfft(int M, int variant, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch_queue_residual(int M, int variant, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch_queue_update(int M, int variant, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch2_queue_rfft(int M, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch2_queue_residual(int M, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch2_queue_update(int M, const WorkQueue &q, cudaStream_t st);
+
 cudaError_t launch_cgemm_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 cudaError_t launch_cgemm_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, int tile = 0);
 cudaError_t gemm_prepare();
@@ -124,12 +145,46 @@ cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st);
 // model spectra written by tc_encode_fwd_map (64-byte aligned host memory)
 cudaError_t tc_encode_fwd_map(void *map_out, const float2 *Xh, int nr, int nv, int ldr, int nf);
 cudaError_t launch_tc_fwd_stream(const GemmArgs &a, const void *map, int nf, cudaStream_t st);
-cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st);
+// map (or null): the 128-byte tensor map of the output (tc_encode_fwd_map of the model-spectra buffer):
+// the tile without reciprocity is then written by the tensor memory accelerator
+cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, const void *map = nullptr);
+// work-queue forms of the tensor-core tile products (persistent CTAs, TMEM allocated once per CTA);
+// tile counts per problem: tc_fwd_tiles (NB = tc_fwd_queue_nb(nb) for every member of a launch),
+// tc_adj_tiles (which also sets the record's tiles_v / tiles_r)
+int tc_fwd_queue_nb(int nb);
+int tc_fwd_tiles(const GemmArgs &a, int nf);
+int tc_adj_tiles(GemmArgs &a, bool recip, int nf);
+cudaError_t launch_tc_fwd_queue(int NB, const WorkQueue &q, cudaStream_t st);
+cudaError_t launch_tc_adj_queue(bool recip, const WorkQueue &q, cudaStream_t st);
 
 // plan internals used by the batch runner (api.cu)
 struct PlanShape {
     int nt, nr, nv, ns, nbmax, nfft, nf, prec, device;
 };
+
+// The launches of one SGD step of a plan (smdd_step with KEEP_XHAT, and REUSE_XHAT unless `first`) as
+// argument records with their tile counts, for the work-queue epochs: the model transform (used on the
+// first step only), the forward product on the tensor-core tile kernel with batch block fwd_nb, the
+// residual step, the adjoint product (tile kernel, reciprocity flag) and the update.  The trace kernels
+// run FFT variant `variant` of complex length M.  Returns MDC_ERR_UNSUPPORTED unless the plan's products
+// run on the tensor cores (MDC_PREC_BF16X3 with MDC_GEMM_TC or MDC_GEMM_TC_STREAM forward and
+// MDC_GEMM_TC adjoint) and no band limit is set.
+struct StepRecords {
+    int M, variant;
+    FftArgs rfft;
+    int rfft_tiles;
+    GemmArgs fwd;
+    int fwd_nb, fwd_tiles;
+    FftArgs resid;
+    int resid_tiles;
+    GemmArgs adj;
+    int adj_tiles;
+    bool recip;
+    FftArgs upd;
+    int upd_tiles;
+};
+int plan_step_records(mdc_plan_s *p, float *X, const float *U_obs, const int32_t *idx, int nb, float alpha, int flags,
+                      double *loss, StepRecords *r);
 PlanShape plan_shape(const mdc_plan_s *p);
 bool plan_begin_capture(mdc_plan_s *p);               // returns the profiling flag it switched off
 void plan_end_capture(mdc_plan_s *p, bool profiling);

@@ -258,6 +258,60 @@ def test_batched_epochs_equal_separate_steps_and_oracle():
     batch.close()
 
 
+@pytest.mark.parametrize("fwd", [binding.MDC_GEMM_TC, binding.MDC_GEMM_TC_STREAM])
+def test_queue_epochs_equal_branch_epochs(fwd):
+    """The work-queue layout (waves of persistent kernels taking (problem, tile) items) runs the same steps
+    with the same arithmetic as the branch layout: models and step losses equal bit for bit after three
+    epochs, on split-BF16 plans of uneven sizes (FFT lengths 256 .. 2048, one with reciprocity, mixed FFT
+    variants), and within 1e-3 of the oracle's trajectories (the split-BF16 bar of the trajectory test)."""
+    n_epochs, n_perm = 3, 2
+    runs = {}
+    for mode in (binding.MDC_BATCH_BRANCHES, binding.MDC_BATCH_QUEUE):
+        members, data = [], []
+        for k, shape in enumerate(MEMBERS):
+            nt, nr, nv, ns, nb, recip = shape
+            D, U_obs, perm, alpha, X0 = _member_data(k, shape, n_perm)
+            plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, precision=binding.MDC_PREC_BF16X3)
+            plan.set_config(fft_variant=[0, 1, 2][k % 3], gemm_fwd=fwd, gemm_adj=binding.MDC_GEMM_TC)
+            steps = oracle.steps_per_epoch(ns, nb)
+            members.append(dict(plan=plan, X=_cuda(X0), U_obs=_cuda(U_obs), perm=_cuda(perm, torch.int32), nb=nb,
+                                alpha=alpha, flags=binding.SMDD_RECIPROCITY if recip else 0,
+                                loss=torch.full((n_epochs, steps), -1.0, device="cuda", dtype=torch.float64)))
+            data.append((D, U_obs, perm, alpha, X0, recip, steps))
+        batch = binding.MDCBatch(members, n_branches=3, mode=mode)
+        if mode == binding.MDC_BATCH_QUEUE:
+            assert batch.kernels_per_epoch < 2 + sum(4 * s + 1 for s in batch.steps)
+        batch.run(0, n_epochs)
+        torch.cuda.synchronize()
+        for m in members:
+            assert m["plan"].sync_status() == binding.MDC_OK
+        runs[mode] = ([m["X"].clone() for m in members], [m["loss"].clone() for m in members], data)
+        batch.close()
+    Xb, Lb, data = runs[binding.MDC_BATCH_BRANCHES]
+    Xq, Lq, _ = runs[binding.MDC_BATCH_QUEUE]
+    for k in range(len(MEMBERS)):
+        assert torch.equal(Xq[k], Xb[k]), f"member {k}: queue model differs from the branch model"
+        assert torch.equal(Lq[k], Lb[k]), f"member {k}: queue losses differ"
+        D, U_obs, perm, alpha, X0, recip, steps = data[k]
+        nb = MEMBERS[k][4]
+        batches = [[perm[e % n_perm][s * nb:(s + 1) * nb] for s in range(steps)] for e in range(n_epochs)]
+        X_ref, _ = oracle.run_epochs(D, X0, U_obs, batches, alpha, recip=recip, fft=True)
+        assert oracle.rel_l2(Xq[k].double().cpu().numpy(), X_ref) <= 1e-3, f"member {k}"
+
+
+def test_queue_mode_requires_tensor_core_products():
+    nt, nr, nv, ns, nb, _ = MEMBERS[0]
+    plan = binding.MDCPlan(_cuda(synth.random_traces((ns, nr, nt), 3)), nv, nb_max=nb)   # FP32 plan
+    m = dict(plan=plan, X=torch.zeros((nv, nr, nt), device="cuda"), U_obs=torch.zeros((ns, nv, nt), device="cuda"),
+             perm=torch.arange(ns, device="cuda", dtype=torch.int32)[None], nb=nb, alpha=0.1)
+    with pytest.raises(binding.MDCError) as e:
+        binding.MDCBatch([m], mode=binding.MDC_BATCH_QUEUE)
+    assert e.value.status == binding.MDC_ERR_UNSUPPORTED
+    with pytest.raises(binding.MDCError) as e:
+        binding.MDCBatch([m], mode=7)
+    assert e.value.status == binding.MDC_ERR_INVALID_ARG
+
+
 def test_batch_replay_is_repeatable_and_reports_index_errors():
     shape = MEMBERS[1]
     nt, nr, nv, ns, nb, _ = shape
