@@ -780,9 +780,6 @@ def solver_comparison(args, dev, D, U_obs, X_true, w, rank):
 # ------------------------------------------------------------------------------------------------
 # GPU arm, many independent problems: whole epochs of every member replayed from one CUDA graph
 # ------------------------------------------------------------------------------------------------
-BATCH_WORKLOAD = "smdd_batch48_nb32"
-
-
 def oracle_member_sample(m, target_s, seed=0):
     """Time the oracle's forward + adjoint of one SGD step of batch member m (nt, nr, nv, nb) on a sample of
     virtual-source columns sized to about target_s, extrapolated linearly in the column count.  The
@@ -809,6 +806,13 @@ def oracle_member_sample(m, target_s, seed=0):
     return step_flops(nt, nr, nv, nb) / t_step / 1e9, t_step, k
 
 
+def largest_shape(args):
+    """(nt, nr, nv, ns) of the batch's fixed largest member, or None."""
+    if not args.batch_largest:
+        return None
+    return tuple(int(v) for v in args.batch_largest_shape.split(","))
+
+
 def run_gpu_batch(args, rank, world):
     import torch
 
@@ -823,7 +827,7 @@ def run_gpu_batch(args, rank, world):
         torch.distributed.barrier()
     binding.load_library()
     specs = synth.batch_members(args.batch_n, seed=1000 + 100000 * rank,
-                                largest=(1500, 1200, 1200, 1200) if args.batch_largest else None)
+                                largest=largest_shape(args))
     tc = args.precision == "bf16x3"
     prec = binding.MDC_PREC_BF16X3 if tc else binding.MDC_PREC_FP32
     n_perm = args.warmup + args.steps
@@ -941,7 +945,8 @@ def run_gpu_batch(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if not tc else "f32 FFTs, bf16x3 (split hi+lo) tensor-core products",
         "data": "synthetic (seeded Ricker/hyperbola generator per member, evaluated on the device; U_obs = GPU forward)",
-        "config": {"workload": BATCH_WORKLOAD, "members": len(specs), "largest_member": bool(args.batch_largest),
+        "config": {"workload": BATCH_WORKLOAD, "members": len(specs),
+                   "largest_member": list(largest_shape(args)) if args.batch_largest else False,
                    "steps_per_epoch_all_members": sum(sp["steps"] for sp in setup), "nb": 32,
                    "precision": args.precision, "a_step_of_this_line": "one epoch of every member (one graph replay)",
                    "branches": batch.n_branches, "kernels_per_epoch": batch.kernels_per_epoch,
@@ -1032,7 +1037,7 @@ def run_reference_batch(args, rank, world):
     if rank != 0:
         return None
     import oracle
-    specs = synth.batch_members(args.batch_n, seed=1000, largest=(1500, 1200, 1200, 1200) if args.batch_largest else None)
+    specs = synth.batch_members(args.batch_n, seed=1000, largest=largest_shape(args))
     for m in specs:
         m["steps"] = -(-m["ns"] // m["nb"])
     order = sorted(specs, key=lambda m: -step_flops(m["nt"], m["nr"], m["nv"], m["nb"]))
@@ -1122,6 +1127,9 @@ def main():
     ap.add_argument("--batch-n", type=int, default=48, help=f"{BATCH_WORKLOAD}: number of members")
     ap.add_argument("--batch-largest", type=int, default=1,
                     help=f"{BATCH_WORKLOAD}: 1 = the last member is the fixed largest one (nt 1500, 1200^3)")
+    ap.add_argument("--batch-largest-shape", default="1500,1200,1200,1200",
+                    help=f"{BATCH_WORKLOAD}: nt,nr,nv,ns of the fixed largest member (a smaller one, with --batch-n 1, "
+                         "makes a single-member run small enough for a multi-pass ncu capture)")
     ap.add_argument("--branches", type=int, default=8, help=f"{BATCH_WORKLOAD}: parallel graph branches")
     ap.add_argument("--batch-mode", default="branches", choices=["branches", "queue"],
                     help=f"{BATCH_WORKLOAD}: epoch layout of the timed run (the other one is timed beside it)")

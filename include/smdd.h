@@ -250,7 +250,7 @@ typedef struct {
     int gemm_fwd;      /* MDC_GEMM_SIMT, MDC_GEMM_TC, MDC_GEMM_GEMV or MDC_GEMM_TC_STREAM */
     int gemm_adj;      /* MDC_GEMM_SIMT, MDC_GEMM_SIMT32, MDC_GEMM_SIMT64 or MDC_GEMM_TC */
     int fft_prefetch;  /* 1: the update runs as persistent CTAs that prefetch the next tile's gradient
-                          spectra while transforming the current one (variants 0 and 1, nfft <= 2048;
+                          spectra while transforming the current one (variants 0 and 1, nfft <= 3072;
                           elsewhere 0) */
     int reserved[4];   /* zero */
 } mdc_config;

@@ -78,7 +78,7 @@ struct mdc_plan_s {
     long long launches = 0;
     // kernel configuration (see mdc_config)
     int fft_variant = 0;
-    int fft_prefetch = 0;        // update: persistent CTAs prefetching the next tile (variants 0/1, M <= 1024)
+    int fft_prefetch = 0;        // update: persistent CTAs prefetching the next tile (variants 0/1, M <= 1536)
     int gemm_fwd = MDC_GEMM_SIMT;
     int gemm_adj = MDC_GEMM_SIMT;
     int nf_active = 0;           // band limit of the products (0: every bin)
@@ -879,7 +879,7 @@ int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
     if (cfg->gemm_fwd == MDC_GEMM_TC_STREAM && !p->xh_map_ok) return MDC_ERR_UNSUPPORTED;
     // the spectra a plan holds are the same for both radix orders: switching keeps them valid
     p->fft_variant = fft_has_variant(p->M, cfg->fft_variant) ? cfg->fft_variant : 0;
-    p->fft_prefetch = (p->M <= 1024 && p->fft_variant != 2) ? cfg->fft_prefetch : 0;
+    p->fft_prefetch = (fft_pf_supported(p->M) && p->fft_variant != 2) ? cfg->fft_prefetch : 0;
     p->gemm_fwd = cfg->gemm_fwd;
     p->gemm_adj = cfg->gemm_adj;
     return MDC_OK;
@@ -942,7 +942,7 @@ int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *bes
         int best_pf = 0;
         for (int cand = 0; cand < 5 && rc == MDC_OK; ++cand) {
             const int v = cand < 2 ? cand : cand < 4 ? cand - 2 : 2, pf = (cand >= 2 && cand < 4) ? 1 : 0;
-            if (!fft_has_variant(p->M, v) || (pf && p->M > 1024)) continue;
+            if (!fft_has_variant(p->M, v) || (pf && !fft_pf_supported(p->M))) continue;
             p->fft_variant = v;
             p->fft_prefetch = pf;
             // a step's two trace kernels: the fused update (scaled from the model subset to every model

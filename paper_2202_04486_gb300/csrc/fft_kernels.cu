@@ -538,10 +538,17 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_q(Wo
 }
 
 // ------------------------------------------------------------------------------------------------
-// persistent update with a prefetched next tile (M <= 1024): each CTA walks the tiles blockIdx.x,
+// persistent update with a prefetched next tile (two tile buffers within 227 KB of shared memory:
+// M <= 1536): each CTA walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...; while it transforms one tile, cp.async copies the next tile's gradient
 // spectra into its second buffer, so the CTA keeps HBM reads in flight through its compute phase.
 // ------------------------------------------------------------------------------------------------
+// two tile buffers of the persistent update fit in a CTA's shared memory (227 KB)
+template <int M>
+__host__ __device__ constexpr bool pf_fits() {
+    return 2 * Team<M>::SMEM <= 232448;
+}
+
 template <int M>
 __device__ __forceinline__ TileCoord coord_at(const TraceGrid &g, int tile, int tr) {
     constexpr int TR = Team<M>::TR;
@@ -578,23 +585,6 @@ __device__ __forceinline__ void tile_prefetch_spec(float2 *buf, const float2 *__
     }
     if (f0 == 0) cp_async8(b + padi(M), c.valid ? s + (long long)M * g.ssf : spec, nbytes);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-template <int M>
-__device__ __forceinline__ void tile_store_spec_at(const float2 *sm, float2 *__restrict__ spec, const TraceGrid &g, int tile) {
-    constexpr int TR = Team<M>::TR, STR = Team<M>::STRIDE, P = Team<M>::P, T = Team<M>::T;
-    const int tr = threadIdx.x % TR, f0 = threadIdx.x / TR;
-    const TileCoord c = coord_at<M>(g, tile, tr);
-    if (!c.valid) return;
-    const float2 *b = sm + tr * STR;
-    float2 *s = spec + (long long)c.i * g.ssi + (long long)c.j * g.ssj;
-#pragma unroll
-    for (int it = 0; it < P; ++it) {
-        const int f = f0 + it * T;
-        const float2 v = (f == 0) ? make_float2(b[0].x, 0.f) : b[padi(f)];
-        s[(long long)f * g.ssf] = v;
-    }
-    if (f0 == 0) s[(long long)M * g.ssf] = make_float2(b[0].y, 0.f);
 }
 
 template <int M, int V, bool KEEP>
@@ -646,7 +636,7 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
             team_sync<T>();
             rfft_regs_to_smem<M, V>(v, buf, t, a.tw, a.twN);
             __syncthreads();
-            tile_store_spec_at<M>(cur, a.spec, a.g, tile);
+            tile_store_spec<M>(cur, a.spec, a.g, tile);
         }
     }
 }
@@ -674,6 +664,21 @@ static int blocks_for(const TraceGrid &g) {
     const int ti = 1 << g.ti_log2, tj = Team<M>::TR >> g.ti_log2;
     if (tj < 1) return -1;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
+}
+
+bool fft_pf_supported(int M) {
+    switch (M) {
+        case 32: return pf_fits<32>();
+        case 64: return pf_fits<64>();
+        case 128: return pf_fits<128>();
+        case 256: return pf_fits<256>();
+        case 512: return pf_fits<512>();
+        case 1024: return pf_fits<1024>();
+        case 1536: return pf_fits<1536>();
+        case 2048: return pf_fits<2048>();
+        case 4096: return pf_fits<4096>();
+    }
+    return false;
 }
 
 int fft_traces_per_cta(int M) {
@@ -768,7 +773,7 @@ static cudaError_t prepare_m() {
         });
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update<M, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if constexpr (M <= 1024) {
+    if constexpr (pf_fits<M>()) {
         for (int v = 0; v < 2; ++v)
             with_variant<M>(v, [&](auto vc) {
                 constexpr int V = decltype(vc)::value;
@@ -826,11 +831,11 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
     return cudaGetLastError();
 }
 
-// the persistent prefetching update (M <= 1024): as many CTAs as fit on the GPU at once, each walking
-// the tiles; returns false (nothing launched) for larger M
+// the persistent prefetching update: as many CTAs as fit on the GPU at once, each walking the tiles;
+// returns false (nothing launched) where two tile buffers do not fit
 template <int M>
 static bool launch_update_pf(bool keep, const FftArgs &a, int ntiles, cudaStream_t st) {
-    if constexpr (M <= 1024) {
+    if constexpr (pf_fits<M>()) {
         with_variant<M>(a.variant, [&](auto vc) {
             constexpr int V = decltype(vc)::value;
             auto kern = keep ? k_update_pf<M, V, true> : k_update_pf<M, V, false>;

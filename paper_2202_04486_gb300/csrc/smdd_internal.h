@@ -102,6 +102,7 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
 cudaError_t launch_update(int M, bool keep_xhat, const FftArgs &a, cudaStream_t st);
 int fft_blocks(int M, const TraceGrid &g);
 int fft_traces_per_cta(int M);
+bool fft_pf_supported(int M);   // the persistent prefetching update exists for complex length M
 cudaError_t fft_prepare(int M);                                // opt-in to the dynamic shared memory of size M
 int fft_tw_size(int M, int variant = 0);
 bool fft_has_variant(int M, int variant);                     // variant 1 exists where it differs from 0

@@ -61,6 +61,34 @@ VARIANT_SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("shape", [
+    (1500, 48, 44, 20, 4),    # nfft 3072: 264 tiles of 8 traces, more than one per persistent CTA
+    (600, 64, 70, 20, 4),     # nfft 2048: 1120 tiles of 4 traces
+    (1023, 40, 41, 12, 3),    # nfft 2048, odd nt, a ragged last tile
+], ids=lambda s: "x".join(map(str, s)))
+def test_prefetch_update_walks_many_tiles(shape, order):
+    """The persistent prefetching update when every CTA walks several tiles (the double buffer
+    alternates): two fused steps against the oracle's SGD steps."""
+    nt, nr, nv, ns, nb = shape
+    seed = sum(shape) + order
+    D = _f32(synth.random_traces((ns, nr, nt), seed))
+    X = _f32(synth.random_traces((nv, nr, nt), seed + 1))
+    U_obs = _f32(synth.random_traces((ns, nv, nt), seed + 2))
+    plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb)
+    plan.set_config(fft_variant=order, fft_prefetch=1)
+    assert plan.get_config()["fft_prefetch"] == 1
+    alpha = 0.3 / oracle.sigma2_max(D)
+    Xg, Ug, Xr = _cuda(X), _cuda(U_obs), X.copy()
+    for k in range(2):
+        ii = synth.random_indices(ns, nb, seed + 3 + k)
+        fl = binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+        binding.smdd_step(plan.handle, Xg, Ug, _cuda(ii, torch.int32), alpha, fl)
+        Xr, _ = oracle.sgd_step(D, Xr, U_obs, ii, alpha)
+    assert plan.sync_status() == binding.MDC_OK
+    _check(Xg.cpu().numpy(), Xr, f"X after two steps {shape}")
+
+
 @pytest.mark.parametrize("variant", [1, 2, "prefetch0", "prefetch1"])
 @pytest.mark.parametrize("shape", VARIANT_SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_fft_variants_match_oracle(shape, variant):
@@ -75,7 +103,7 @@ def test_fft_variants_match_oracle(shape, variant):
     if isinstance(variant, str):   # the persistent prefetching update with radix order 0 or 1
         order = int(variant[-1])
         plan.set_config(fft_variant=order, fft_prefetch=1)
-        assert plan.get_config()["fft_prefetch"] == (1 if M <= 1024 else 0)
+        assert plan.get_config()["fft_prefetch"] == (1 if M <= 1536 else 0)
     else:
         plan.set_config(fft_variant=variant)
         # variant 1 falls back to 0 where both radix orders coincide; variant 2 exists for 128 <= M <= 1024
