@@ -81,29 +81,44 @@ def fft_flops(nt: int) -> float:
     return 2.5 * n * math.log2(n)
 
 
-def step_work(nt, nr, nv, nb) -> tuple[float, float]:
-    """(F_gemm, F_fft) of one SGD step."""
-    return 16.0 * nb * nr * nv * nf_of(nt), 2.0 * fft_flops(nt) * (nr * nv + nb * nv)
+def model_traces(nr, nv, sym=False) -> int:
+    """Distinct model traces: nr nv, or nv (nv + 1) / 2 for a symmetric model (reciprocity, Eq. 4: the
+    model X = C_r z is symmetric, so the traces on and above the diagonal determine it)."""
+    return nv * (nv + 1) // 2 if sym else nr * nv
 
 
-def step_flops(nt, nr, nv, nb) -> float:
-    return sum(step_work(nt, nr, nv, nb))
+def step_work(nt, nr, nv, nb, sym=False) -> tuple[float, float]:
+    """(F_gemm, F_fft) of one SGD step (sym: the model transforms of the distinct traces only)."""
+    return 16.0 * nb * nr * nv * nf_of(nt), 2.0 * fft_flops(nt) * (model_traces(nr, nv, sym) + nb * nv)
 
 
-def step_bytes_compulsory(nt, nr, nv, nb, recip) -> float:
+def step_flops(nt, nr, nv, nb, sym=False) -> float:
+    return sum(step_work(nt, nr, nv, nb, sym))
+
+
+def step_bytes_compulsory(nt, nr, nv, nb, recip, sym=False) -> float:
     """Model read + write, the gathered kernel spectra, the batch rows of U_obs (and, with reciprocity,
-    the round trip of the gradient that couples trace (r, v) with (v, r))."""
+    the round trip of the gradient that couples trace (r, v) with (v, r)).  sym: a symmetric model is read
+    on its distinct traces and written whole; the symmetric gradient is formed in the adjoint product, so
+    there is no gradient round trip."""
+    if sym:
+        return float((model_traces(nr, nv, True) + nr * nv) * nt * 4 + nf_of(nt) * nb * nr * 8 + nb * nv * nt * 4)
     b = 2 * nr * nv * nt * 4 + nf_of(nt) * nb * nr * 8 + nb * nv * nt * 4
     if recip:
         b += 2 * nr * nv * nt * 4
     return float(b)
 
 
-def kernel_work(stage, nt, nr, nv, nb):
+def kernel_work(stage, nt, nr, nv, nb, sym=False):
     """Algorithmic bytes and flops of one launch of a stage, and the bytes the staged pipeline moves in
-    addition (spectra written by one kernel and read by the next), at the algorithmic FFT length."""
+    addition (spectra written by one kernel and read by the next), at the algorithmic FFT length.  sym: the
+    update of a symmetric model (its distinct traces transformed, the model written whole, the spectra below
+    the block diagonal copied from above it)."""
     nf = nf_of(nt)
     ff = fft_flops(nt)
+    if stage == "update" and sym:
+        up, low = model_traces(nr, nv, True), nr * nv - model_traces(nr, nv, True)
+        return dict(bytes=(up + nr * nv) * nt * 4, flops=2 * ff * up, staged=2 * (up + low) * nf * 8, tensor=False)
     if stage == "update":      # inverse FFT of the gradient, update, FFT of the new model, per model trace
         return dict(bytes=2 * nv * nr * nt * 4, flops=2 * ff * nv * nr, staged=2 * nv * nr * nf * 8, tensor=False)
     if stage == "cgemm_fwd":   # products with the gathered kernel rows; model spectra in, batch spectra out
@@ -170,11 +185,11 @@ class Peaks:
         roof["staged_gbs"] = round((work["bytes"] + work["staged"]) / t / 1e9, 1)
         return roof
 
-    def step_roof_s(self, nt, nr, nv, nb, recip, tensor_products: bool) -> float:
+    def step_roof_s(self, nt, nr, nv, nb, recip, tensor_products: bool, sym=False) -> float:
         """T_roof of one step: max(B / HBM, F_gemm / P_gemm + F_fft / P_FP32)."""
-        fg, ff = step_work(nt, nr, nv, nb)
+        fg, ff = step_work(nt, nr, nv, nb, sym)
         p_gemm = self.bf16 if tensor_products else self.fp32
-        return max(step_bytes_compulsory(nt, nr, nv, nb, recip) / self.hbm, fg / p_gemm + ff / self.fp32)
+        return max(step_bytes_compulsory(nt, nr, nv, nb, recip, sym) / self.hbm, fg / p_gemm + ff / self.fp32)
 
 
 def kernel_source_hash() -> str:
@@ -329,7 +344,7 @@ def time_oracle(w, D, X, U_obs, batches, target_s=12.0, max_cols=None):
     oracle_step_sample(D, X, U_obs, idx, vsel)
     t1 = time.perf_counter()
     t_step = (t1 - t0) * nv / k
-    f = step_flops(w["nt"], w["nr"], w["nv"], len(idx))
+    f = step_flops(w["nt"], w["nr"], w["nv"], len(idx), bool(w["reciprocity"]))
     sample = (f"forward+adjoint direct sums (FP64) for {k} of {nv} virtual-source columns of one batch of "
               f"{len(idx)} sources, extrapolated linearly in the column count ({t1 - t0:.1f} s measured)")
     return f / t_step / 1e9, t_step, sample, oracle.num_threads()
@@ -356,7 +371,7 @@ def oracle_extra(w, D, X, U_obs, idx, target_s=3.0):
         oracle.set_num_threads(cores)
     macs = 2.0 * len(idx) * w["nv"] * w["nr"] * w["nt"] * (w["nt"] + 1) / 2   # forward + adjoint direct sums
     res["tier_a_1thread_s_per_step"] = round(t1, 3)
-    res["tier_a_1thread_gflops"] = round(step_flops(w["nt"], w["nr"], w["nv"], len(idx)) / t1 / 1e9, 5)
+    res["tier_a_1thread_gflops"] = round(step_flops(w["nt"], w["nr"], w["nv"], len(idx), bool(w["reciprocity"])) / t1 / 1e9, 5)
     res["tier_a_1thread_direct_mac_per_s"] = round(macs / t1, 1)
     t0 = time.perf_counter()
     k = max(1, min(nv, 4))
@@ -383,14 +398,14 @@ def measured_peaks(dev):
     return Peaks(binding.alu_peak_tflops(0), fp32_derived), binding.alu_peak_tflops(1)
 
 
-def stage_roofs(peaks, stage, member, tensor_products):
+def stage_roofs(peaks, stage, member, tensor_products, sym=False):
     """Per-stage roofline of the timed steps: stage -> (ms, launches) from the library's stage timers."""
     nt, nr, nv, nb = member
     out = {}
     for k, (ms, n) in stage.items():
         if n <= 0 or k not in ("rfft", "cgemm_fwd", "residual", "cgemm_adj", "update"):
             continue
-        out[k] = peaks.kernel_roof(k, kernel_work(k, nt, nr, nv, nb), ms / n, tensor_products)
+        out[k] = peaks.kernel_roof(k, kernel_work(k, nt, nr, nv, nb, sym), ms / n, tensor_products)
         out[k]["launches"] = int(n)
     tot = sum(v["launch_ms"] * v["launches"] for v in out.values())
     for v in out.values():
@@ -431,7 +446,8 @@ def run_gpu(args, rank, world, w):
     chosen = plan.autotune(nb, binding.SMDD_RECIPROCITY if recip else 0, reps=5) if args.autotune else plan.get_config()
     sigma2 = plan.sigma2_max(60)
     alpha = 0.5 * 2.0 / sigma2
-    flags = (binding.SMDD_RECIPROCITY if recip else 0) | binding.SMDD_KEEP_XHAT
+    # the model starts at zero, so with reciprocity it stays symmetric: the update runs on its distinct traces
+    flags = ((binding.SMDD_RECIPROCITY | binding.SMDD_SYMMETRIC) if recip else 0) | binding.SMDD_KEEP_XHAT
     X = torch.zeros((nv, nr, nt), device=dev)
     n_ep = 2 * (args.warmup + args.steps) // math.ceil(ns / nb) + 3
     batches = [b for ep in synth.epoch_batches(ns, nb, n_ep, seed=rank) for b in ep]
@@ -442,7 +458,7 @@ def run_gpu(args, rank, world, w):
     # unless the step's own traffic is far larger than L2 (then back-to-back steps, as an SGD run issues
     # them, and the inputs themselves evict L2)
     l2_bytes = 126 * 1024 * 1024
-    step_traffic = step_bytes_compulsory(nt, nr, nv, nb, recip) + 4.0 * nf_of(nt) * nv * nr * 8
+    step_traffic = step_bytes_compulsory(nt, nr, nv, nb, recip, recip) + 4.0 * nf_of(nt) * nv * nr * 8
     do_flush = args.l2 == "flush" or (args.l2 == "auto" and step_traffic < 4 * l2_bytes)
     stream = torch.cuda.current_stream()
 
@@ -485,7 +501,7 @@ def run_gpu(args, rank, world, w):
         raise RuntimeError(f"device status {binding.status_string(status)}")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(step_ms) / 1e3
-    flops = sum(step_flops(nt, nr, nv, len(batches[args.warmup + i])) for i in range(args.steps))
+    flops = sum(step_flops(nt, nr, nv, len(batches[args.warmup + i]), recip) for i in range(args.steps))
     losses = loss[: args.warmup + args.steps].cpu().numpy()
 
     # stage shares: the same steps once more with the library's per-kernel CUDA events (outside the timed
@@ -545,11 +561,11 @@ def run_gpu(args, rank, world, w):
         return None
 
     peaks, fp64_peak = measured_peaks(dev)
-    kern = stage_roofs(peaks, stage, (nt, nr, nv, nb), tc)
+    kern = stage_roofs(peaks, stage, (nt, nr, nv, nb), tc, recip)
     dom = max(kern, key=lambda k: kern[k]["share"])
     roof = dict(kern[dom])
     roof["traffic"] = ncu_traffic(dom, args.workload)
-    t_roof = peaks.step_roof_s(nt, nr, nv, nb, recip, tc)
+    t_roof = peaks.step_roof_s(nt, nr, nv, nb, recip, tc, recip)
     ms_per_step = t_dev / args.steps * 1e3
     nfft_impl, _ = binding.mdc_plan_info(plan.handle)
 
@@ -803,7 +819,7 @@ def oracle_member_sample(m, target_s, seed=0):
     k = int(min(nv, max(1, target_s / per_col)))
     t = run(k) if k > 1 else per_col
     t_step = t * nv / k
-    return step_flops(nt, nr, nv, nb) / t_step / 1e9, t_step, k
+    return step_flops(nt, nr, nv, nb, m["reciprocity"]) / t_step / 1e9, t_step, k
 
 
 def largest_shape(args):
@@ -844,7 +860,8 @@ def run_gpu_batch(args, rank, world):
             plan.forward(Xt, ii, out=U_obs[s0:s0 + ii.numel()])
         del D, Xt
         alpha = 0.5 * 2.0 / plan.sigma2_max(30)
-        flags = binding.SMDD_RECIPROCITY if m["reciprocity"] else 0
+        # every member starts at X = 0: a reciprocity member stays symmetric (update on its distinct traces)
+        flags = (binding.SMDD_RECIPROCITY | binding.SMDD_SYMMETRIC) if m["reciprocity"] else 0
         cfg = plan.autotune(nb, flags, reps=3) if args.autotune else plan.get_config()
         perm = np.stack([np.concatenate(ep) for ep in synth.epoch_batches(ns, nb, n_perm, seed=m["seed"])])
         steps = -(-ns // nb)
@@ -859,7 +876,7 @@ def run_gpu_batch(args, rank, world):
     batch = binding.MDCBatch(members, n_branches=args.branches, mode=mode)
     step_sizes = [(m["nt"], m["nr"], m["nv"], min(m["nb"], m["ns"] - s * m["nb"]), m["reciprocity"])
                   for m in setup for s in range(m["steps"])]
-    epoch_flops = sum(step_flops(nt, nr, nv, nb) for nt, nr, nv, nb, _ in step_sizes)
+    epoch_flops = sum(step_flops(nt, nr, nv, nb, rc) for nt, nr, nv, nb, rc in step_sizes)
     stream = torch.cuda.current_stream()
 
     batch.run(0, args.warmup)
@@ -908,7 +925,8 @@ def run_gpu_batch(args, rank, world):
     t_e2e = time.perf_counter() - e0
 
     # per-kernel figures of the largest member, from a few profiled steps outside the graph
-    big = max(range(len(setup)), key=lambda k: step_flops(setup[k]["nt"], setup[k]["nr"], setup[k]["nv"], setup[k]["nb"]))
+    big = max(range(len(setup)), key=lambda k: step_flops(setup[k]["nt"], setup[k]["nr"], setup[k]["nv"], setup[k]["nb"],
+                                                          setup[k]["reciprocity"]))
     mb, sb = members[big], setup[big]
     plan = mb["plan"]
     binding.mdc_plan_set_profiling(plan.handle, True)
@@ -926,12 +944,12 @@ def run_gpu_batch(args, rank, world):
     if rank != 0:
         return None
     peaks, fp64_peak = measured_peaks(dev)
-    kern = stage_roofs(peaks, stage, (sb["nt"], sb["nr"], sb["nv"], sb["nb"]), tc)
+    kern = stage_roofs(peaks, stage, (sb["nt"], sb["nr"], sb["nv"], sb["nb"]), tc, sb["reciprocity"])
     dom = max(kern, key=lambda k: kern[k]["share"])
     roof = dict(kern[dom])
     roof["traffic"] = ncu_traffic(dom, BATCH_WORKLOAD)
     roof["member"] = {k: sb[k] for k in ("nt", "nr", "nv", "ns", "nb")}
-    t_roof_epoch = sum(peaks.step_roof_s(nt, nr, nv, nb, rc, tc) for nt, nr, nv, nb, rc in step_sizes)
+    t_roof_epoch = sum(peaks.step_roof_s(nt, nr, nv, nb, rc, tc, rc) for nt, nr, nv, nb, rc in step_sizes)
     ms_epoch = t_dev / args.steps * 1e3
     cfgs, nffts = {}, {}
     for sp in setup:
@@ -1040,7 +1058,7 @@ def run_reference_batch(args, rank, world):
     specs = synth.batch_members(args.batch_n, seed=1000, largest=largest_shape(args))
     for m in specs:
         m["steps"] = -(-m["ns"] // m["nb"])
-    order = sorted(specs, key=lambda m: -step_flops(m["nt"], m["nr"], m["nv"], m["nb"]))
+    order = sorted(specs, key=lambda m: -step_flops(m["nt"], m["nr"], m["nv"], m["nb"], m["reciprocity"]))
     budget = 150.0 / max(1, args.steps + args.warmup)
     f_tot = t_tot = 0.0
     used = []
@@ -1049,11 +1067,11 @@ def run_reference_batch(args, rank, world):
         m = order[(k - args.warmup) % len(order)] if k >= args.warmup else order[-1 - k % len(order)]
         val, t_step, cols = oracle_member_sample(m, budget, seed=k)
         if k >= args.warmup:
-            f_tot += m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"])
+            f_tot += m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"], m["reciprocity"])
             t_tot += m["steps"] * t_step
             used.append(f"{m['nt']}/{m['nr']}x{m['nv']}:{cols}")
     val = f_tot / t_tot / 1e9
-    epoch_flops = sum(m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"]) for m in specs)
+    epoch_flops = sum(m["steps"] * step_flops(m["nt"], m["nr"], m["nv"], m["nb"], m["reciprocity"]) for m in specs)
     sample = ("each step: FP64 direct-sum forward + adjoint of one SGD step of one member (largest first, in "
               "turn) on a column sample, extrapolated in the column count; epoch-weighted over the members "
               "timed (nt/nr x nv:columns): " + ", ".join(used) + "; ms_per_step = the epoch of all members at "
@@ -1098,7 +1116,7 @@ def run_reference(args, rank, world, w):
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             t_tot += dt * nv / ncols
-            f_tot += step_flops(nt, nr, nv, len(idx))
+            f_tot += step_flops(nt, nr, nv, len(idx), bool(w["reciprocity"]))
             cols_used.append(ncols)
     val = f_tot / t_tot / 1e9
     sample = (f"each step: FP64 direct-sum forward+adjoint on {min(cols_used)}-{max(cols_used)} of {nv} "

@@ -112,6 +112,14 @@ int mdc_adjoint(mdc_plan_t plan, const float *R, const int32_t *idx, int nb, flo
                                    same X pointer (the caller promises X was not modified in between;
                                    ignored if the plan holds no spectrum for this pointer) */
 #define SMDD_UOBS_GATHERED  8   /* U_obs is [nb][nv][nt]: the batch rows, already gathered */
+#define SMDD_SYMMETRIC      64  /* with SMDD_RECIPROCITY (smdd_step, smdd_step_host, batched epochs): the caller
+                                   promises X[v][r] == X[r][v] on entry -- a symmetric start stays symmetric
+                                   under C_r (Eq. 4, X = C_r z) -- so the update transforms only the traces on
+                                   and above the diagonal (in blocks of the FFT kernels' traces per CTA) and
+                                   writes each result to both (v, r) and (r, v); the result is identical to the
+                                   step without the flag on a symmetric X.  On a non-symmetric X the lower
+                                   triangle is overwritten by the mirrored upper one.  Without
+                                   SMDD_RECIPROCITY it is ignored. */
 
 typedef struct {
     float alpha;        /* step size (Appendix B: a fraction of 2 / sigma^2) */
@@ -135,7 +143,7 @@ int smdd_step(mdc_plan_t plan, float *X, const float *U_obs, const int32_t *idx,
  *                and copied at once, so the caller may reuse it when the call returns.
  *   loss_host  : host float64 written asynchronously with 1/2 ||R||^2 (pinned memory; valid once
  *                `stream` has passed the step), or NULL.
- *   flags      : SMDD_RECIPROCITY, SMDD_KEEP_XHAT, SMDD_REUSE_XHAT.
+ *   flags      : SMDD_RECIPROCITY, SMDD_KEEP_XHAT, SMDD_REUSE_XHAT, SMDD_SYMMETRIC.
  * The plan copies the index list and the nb rows U_obs_host[idx[b]] (consecutive sources as one copy)
  * into one of two device staging slots on a copy stream of its own, then queues the step on `stream`
  * behind them: the copies of a call overlap the step of the previous call, and a slot is refilled only
@@ -298,7 +306,7 @@ typedef struct {
     int n_perm;               /* >= 1 */
     int nb;                   /* batch size, 1 .. nb_max of the plan: ceil(ns / nb) steps per epoch, the last partial */
     float alpha;              /* step size */
-    int flags;                /* 0 or SMDD_RECIPROCITY */
+    int flags;                /* 0, SMDD_RECIPROCITY, or SMDD_RECIPROCITY | SMDD_SYMMETRIC (a symmetric start) */
     double *loss;             /* device float64[loss_rows][ceil(ns/nb)], or NULL: epoch e writes its step
                                  losses 1/2 ||R||^2 into row e % loss_rows */
     int loss_rows;            /* >= 1 when loss is given */

@@ -31,6 +31,7 @@ SMDD_REUSE_XHAT = 4
 SMDD_UOBS_GATHERED = 8
 SMDD_NESTEROV = 16
 SMDD_ADAM = 32
+SMDD_SYMMETRIC = 64
 
 MDC_NUM_STAGES = 7
 
@@ -398,7 +399,8 @@ class MDCBatch:
     """Many independent problems, whole SGD epochs replayed from one captured CUDA graph.
 
     members: list of dicts with keys plan (MDCPlan), X, U_obs, perm (int32 [n_perm][ns]), nb, alpha,
-    flags (0 or SMDD_RECIPROCITY), loss (float64 [loss_rows][steps] or None).  The tensors must stay
+    flags (0, SMDD_RECIPROCITY, or SMDD_RECIPROCITY | SMDD_SYMMETRIC for a model that starts symmetric),
+    loss (float64 [loss_rows][steps] or None).  The tensors must stay
     alive (and at the same addresses) while the batch lives; this object keeps references to them.
     mode: MDC_BATCH_BRANCHES (members on n_branches graph branches) or MDC_BATCH_QUEUE (waves of
     persistent kernels with device work queues; split-BF16 plans with tensor-core products).

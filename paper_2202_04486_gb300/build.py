@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the radix FFT kernels are instantiated one complex length per unit (fft_m*.cu), the slowest to compile first
 SOURCES = ["fft_m4096.cu", "fft_m2048.cu", "fft_m1536.cu", "fft_m1024.cu", "fft_m512.cu", "fft_m_small.cu",
            "fft2_kernels.cu", "fft_kernels.cu", "api.cu", "gemm_kernels.cu", "setup_kernels.cu", "noalloc.cu",
-           "gemm_tc.cu", "batch.cu", "lsqr.cu", "alu_probe.cu"]
+           "gemm_tc.cu", "batch.cu", "lsqr.cu", "alu_probe.cu", "sym_kernels.cu"]
 
 
 def _nvcc() -> str:

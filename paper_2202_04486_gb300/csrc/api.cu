@@ -223,7 +223,7 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_cgemm_fwd(g, p->nf, st); });
 }
 
-int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStream_t st) {
+int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStream_t st, bool no_mirror = false) {
     GemmArgs g;
     memset(&g, 0, sizeof(g));
     g.A = p->Uh;
@@ -238,6 +238,7 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.status = p->status;
     g.nf_active = p->nf_active;
     g.wait_probe = p->wait_probe;
+    g.no_mirror = (recip && no_mirror) ? 1 : 0;
     if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] {
             return launch_tc_adj(g, recip, p->nf, st, (SMDD_TC_ADJ_TMA && p->xh_map_ok) ? p->xh_map : nullptr);
@@ -602,6 +603,17 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
               const AdamArgs &adam = AdamArgs()) {
     int rc = MDC_OK;
     const bool recip = flags & SMDD_RECIPROCITY;
+    const bool ext = vel || mute || adam.m;
+    // the update's FFT plan: the momentum / mute / Adam update and the upper enumeration of a symmetric
+    // model exist for the radix orders only (variant 0 where the plan uses the register FFT)
+    const int v_plan = p->fft_variant;
+    const int v_upd = ext ? 0 : ((recip && (flags & SMDD_SYMMETRIC) && v_plan == 2) ? 0 : v_plan);
+    p->fft_variant = v_upd;
+    const TraceGrid mg = model_grid(p, p->nv);
+    const bool sym = recip && (flags & SMDD_SYMMETRIC) && !ext && (1 << mg.ti_log2) == traces_per_cta(p) &&
+                     traces_per_cta(p) <= 32;
+    const int tr_upd = traces_per_cta(p);
+    p->fft_variant = v_plan;
     // a1: model spectra (or the ones left by the previous step's fused update)
     if (!((flags & SMDD_REUSE_XHAT) && p->xhat_for == X)) {
         if ((rc = rfft_model(p, X, st))) return rc;
@@ -627,18 +639,21 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         if ((rc = launch_stage(p, ST_RESID, st, [&] { return launch_residual(p->M, a, p->resid_blocks_max, st); })))
             return rc;
     }
-    // a6: gradient spectra (with the reciprocity projection folded in)
-    if ((rc = gemm_adjoint(p, idx, nb, recip, st))) return rc;
+    // a6: gradient spectra (with the reciprocity projection folded in; a symmetric model's update reads
+    // the upper triangle only, so the mirrored tiles are not written)
+    if ((rc = gemm_adjoint(p, idx, nb, recip, st, sym))) return rc;
     // a7 + a8: inverse FFT, window, update, and optionally the spectra of the new model
     {
         const bool keep = flags & SMDD_KEEP_XHAT;
-        // the momentum / mute update exists for the default radix order only: lay its grid out (and take
-        // its twiddle table) for FFT variant 0, whatever the plan's variant
-        const int v_plan = p->fft_variant;
-        if (vel || mute || adam.m) p->fft_variant = 0;
+        // grid and twiddle table of the update's FFT plan (v_upd)
+        p->fft_variant = v_upd;
         FftArgs a = base_fft(p);
-        a.g = model_grid(p, p->nv);
+        a.g = mg;
         p->fft_variant = v_plan;
+        if (sym) {
+            a.g.sym = 1;
+            a.prefetch = 0;
+        }
         a.tout = X;
         a.vec = vec4_ok(p->nt, X) && (vel == nullptr || vec4_ok(p->nt, vel)) &&
                 (adam.m == nullptr || (vec4_ok(p->nt, adam.m) && vec4_ok(p->nt, adam.v)));
@@ -654,7 +669,13 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         a.eps = adam.eps;
         a.c1 = adam.c1;
         a.c2 = adam.c2;
-        if ((rc = launch_stage(p, ST_UPDATE, st, [&] { return launch_update(p->M, keep, a, st); }))) return rc;
+        // a symmetric model's spectra below the block diagonal are copies of the ones above it
+        if ((rc = launch_stage(p, ST_UPDATE, st, [&] {
+                 const cudaError_t e = launch_update(p->M, keep, a, st);
+                 if (e != cudaSuccess || !(keep && sym)) return e;
+                 return launch_mirror_lower(p->Xh, p->nv, p->ldr, (long long)p->nv * p->ldr, p->nf, tr_upd, st);
+             })))
+            return rc;
         if (keep) p->xhat_for = X;
     }
     return MDC_OK;
@@ -744,7 +765,8 @@ int smdd_step(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
     if (rc) return rc;
     if (!prm) return MDC_ERR_INVALID_ARG;
     const int flags = prm->flags;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_SYMMETRIC))
+        return MDC_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i)
         if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
     if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
@@ -759,7 +781,7 @@ int smdd_step_host(mdc_plan_t p, float *X, const float *U_host, const int32_t *i
     if (rc) return rc;
     if (!prm) return MDC_ERR_INVALID_ARG;
     const int flags = prm->flags;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT)) return MDC_ERR_INVALID_ARG;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_SYMMETRIC)) return MDC_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i)
         if (prm->reserved[i] != 0) return MDC_ERR_INVALID_ARG;
     if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;
@@ -888,7 +910,8 @@ int mdc_plan_set_config(mdc_plan_t p, const mdc_config *cfg) {
 int mdc_plan_autotune(mdc_plan_t p, int nb, int flags, int reps, mdc_config *best, void *stream) {
     if (!p || nb < 1 || reps < 1) return MDC_ERR_INVALID_ARG;
     if (nb > p->nbmax) return MDC_ERR_SHAPE;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED)) return MDC_ERR_INVALID_ARG;
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_SYMMETRIC))
+        return MDC_ERR_INVALID_ARG;
     const bool recip = flags & SMDD_RECIPROCITY;
     if (recip && p->nr != p->nv) return MDC_ERR_SHAPE;
     if (reps > 100) reps = 100;

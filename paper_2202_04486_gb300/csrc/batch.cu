@@ -164,7 +164,7 @@ int mdc_batch_create_ex(mdc_batch_t *out, const smdd_member *members, int n, int
         if (!mb.plan || !mb.X || !mb.U_obs || !mb.perm || mb.n_perm < 1) return MDC_ERR_INVALID_ARG;
         for (int i = 0; i < 4; ++i)
             if (mb.reserved[i] != 0) return MDC_ERR_INVALID_ARG;
-        if (mb.flags & ~SMDD_RECIPROCITY) return MDC_ERR_INVALID_ARG;
+        if (mb.flags & ~(SMDD_RECIPROCITY | SMDD_SYMMETRIC)) return MDC_ERR_INVALID_ARG;
         if (mb.loss && mb.loss_rows < 1) return MDC_ERR_INVALID_ARG;
         shapes[m] = plan_shape(mb.plan);
         if (shapes[m].device != dev) return MDC_ERR_INVALID_ARG;

@@ -49,6 +49,22 @@ __device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr, int bi
     return c;
 }
 
+// Upper enumeration of a square grid (TraceGrid::sym): tile number bid -> the number of the same tile in
+// the full enumeration (bi + nbi j).  Rows j = TR g .. TR g + TR - 1 form group g, each row holding the
+// tiles bi = g .. nbi - 1, so group g starts at G(g) = TR (g nbi - g (g - 1) / 2).
+__device__ __forceinline__ int sym_tile_to_full(const TraceGrid &g, int TR, int bid) {
+    const int nbi = (g.ni + TR - 1) / TR;
+    auto G = [&](long long q) { return (long long)TR * (q * nbi - q * (q - 1) / 2); };
+    const float h = nbi + 0.5f;
+    int q = (int)(h - sqrtf(fmaxf(h * h - 2.f * (float)bid / (float)TR, 0.f)));
+    q = q < 0 ? 0 : (q > nbi - 1 ? nbi - 1 : q);
+    while (q > 0 && G(q) > bid) --q;
+    while (q + 1 < nbi && G(q + 1) <= bid) ++q;
+    const int off = (int)(bid - G(q)), w = nbi - q;
+    const int j = q * TR + off / w, bi = q + off % w;
+    return j * nbi + bi;
+}
+
 #ifndef SMDD_FFT_PAIR_IO
 #define SMDD_FFT_PAIR_IO 1   // spectrum tiles moved as 16-byte pairs of adjacent traces where the grid allows
 #endif
@@ -346,14 +362,13 @@ __device__ __forceinline__ void residual_body(const FftArgs &a, int bid, int nbl
         }
         if (row >= 0) uo = a.uobs + (long long)row * a.uo_si + (long long)c.j * a.uo_sj;
     }
-    float4 o[NPAIR];
-    load_pairs<M, V>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o);
-
     tile_load_spec<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
-    irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
+    float4 o[NPAIR];   // observed row, loaded after the first inverse pass (its latency overlaps the rest)
+    irfft_smem_to_regs_mid<M, V>(v, buf, t, a.tw, a.twN,
+                                 [&] { load_pairs<M, V>(uo ? uo : a.uobs, a.nt, uo != nullptr, a.vec, t, o); });
 
     double l2 = 0.0;
     float4 z[NPAIR];
@@ -405,21 +420,31 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
 // Update: g = s * irfft(Gh)[0:nt];  X <- X - alpha g (SGD), or with the causality mute and/or Nesterov
 // momentum (see the else branch);  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
+//
+// Symmetric model (a.g.sym, reciprocity on a square grid with X[v][r] = X[r][v]): only the tiles on or above
+// the TR-block diagonal run; a trace (v, r) of a tile above it (r >= TR (v / TR + 1)) also writes its
+// mirror X[r][v], which it equals, and the spectra below the block diagonal are left to
+// launch_mirror_lower.  Traces of the diagonal blocks run in both orders (their mirrors are in the same
+// block row and column), so every element of X is written once.
 template <int M, int V, bool KEEP, bool EXT>
-__device__ __forceinline__ void update_body(const FftArgs &a, int bid) {
+__device__ __forceinline__ void update_body(const FftArgs &a, int bid_in) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
+    const int bid = (!EXT && a.g.sym) ? sym_tile_to_full(a.g, Team<M>::TR, bid_in) : bid_in;
     const TileCoord c = coord_of<M>(a.g, tr, bid);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-    float4 xo[NPAIR];
-    load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo);      // model samples, prefetched
+    // the mirror trace (r, v) of a trace above the block diagonal
+    float *xm = (!EXT && a.g.sym && c.valid && c.i / Team<M>::TR > c.j / Team<M>::TR)
+                    ? a.tout + (long long)c.j * a.g.tsi + (long long)c.i * a.g.tsj
+                    : nullptr;
 
     tile_load_spec<M>(sm, a.spec, a.g, bid);
     __syncthreads();
     float2 *buf = sm + tr * Team<M>::STRIDE;
     float2 v[FFT_P];
-    irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
+    float4 xo[NPAIR];   // model samples, loaded after the first inverse pass (latency overlaps the rest)
+    irfft_smem_to_regs_mid<M, V>(v, buf, t, a.tw, a.twN, [&] { load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo); });
     const float nas = -a.alpha * a.s;
     if constexpr (!EXT) {
         // SGD: X <- X - alpha g
@@ -437,6 +462,7 @@ __device__ __forceinline__ void update_body(const FftArgs &a, int bid) {
                 z.z = (i0 + 2 < a.nt) ? fmaf(nas, g1.x, xv.z) : 0.f;
                 z.w = (i0 + 3 < a.nt) ? fmaf(nas, g1.y, xv.w) : 0.f;
                 if (c.valid) store_quad(x, i0, a.nt, a.vec, z);
+                if (xm) store_quad(xm, i0, a.nt, a.vec, z);
                 xo[hs] = z;
             }
     } else {
@@ -606,8 +632,6 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
         float2 *cur = sm + (it & 1) * BUF;
         const TileCoord c = coord_at<M>(a.g, tile, tr);
         float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
-        float4 xo[NPAIR];
-        load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();   // this tile's spectra have landed; every thread is done with the previous tile
         if (threadIdx.x < TR) {   // slot 0 packs (Re X[0], Re X[M])
@@ -619,7 +643,8 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
         if (nxt < ntiles) tile_prefetch_spec<M>(sm + ((it + 1) & 1) * BUF, a.spec, a.g, nxt);
         float2 *buf = cur + tr * Team<M>::STRIDE;
         float2 v[FFT_P];
-        irfft_smem_to_regs<M, V>(v, buf, t, a.tw, a.twN);
+        float4 xo[NPAIR];
+        irfft_smem_to_regs_mid<M, V>(v, buf, t, a.tw, a.twN, [&] { load_pairs<M, V>(x, a.nt, c.valid, a.vec, t, xo); });
 #pragma unroll
         for (int qq = 0; qq < QQ; ++qq)
 #pragma unroll
@@ -651,9 +676,11 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_update_pf(F
 // ------------------------------------------------------------------------------------------------
 template <int M>
 int blocks_for(const TraceGrid &g) {
-    // -1: the grid was laid out for CTAs of another trace count (more traces along i than a CTA holds)
+    // -1: the grid was laid out for CTAs of another trace count (more traces along i than a CTA holds), or
+    // an upper enumeration of a grid that is not square with whole CTAs along i
     const int ti = 1 << g.ti_log2, tj = Team<M>::TR >> g.ti_log2;
     if (tj < 1) return -1;
+    if (g.sym) return (tj == 1 && g.ni == g.nj) ? (int)sym_tiles(g.ni, Team<M>::TR) : -1;
     return ((g.ni + ti - 1) / ti) * ((g.nj + tj - 1) / tj);
 }
 
@@ -769,7 +796,7 @@ cudaError_t FftLaunch<M>::update(bool keep, const FftArgs &a, cudaStream_t st) {
     const int nb = blocks_for<M>(a.g);
     if (nb < 0) return cudaErrorInvalidValue;
     if (nb == 0) return cudaSuccess;
-    if (a.prefetch && !ext && launch_update_pf<M>(keep, a, nb, st)) {
+    if (a.prefetch && !ext && !a.g.sym && launch_update_pf<M>(keep, a, nb, st)) {
         // persistent, prefetching form launched
     } else if (ext) {
         // momentum / Adam / causality mute: radix order 0 only (the caller passes its twiddle table)

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(AdjGeom<TT>::THREADS, TT == 64 ? 3 : 8) k_cgem
             }
         }
     }
-    if (RECIP) {
+    if (RECIP && (diag || !a.no_mirror)) {   // diagonal tiles always mirror (see GemmArgs::no_mirror)
         __syncthreads();
         for (int e = tid; e < TT * TT; e += G::THREADS) {
             const int rr = e / TT, vv = e % TT;

@@ -515,7 +515,8 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
                 const int row = e >> 6, col = e & 63, v = v0 + row, r = rp + col;
                 if (v < a.nv && r < a.nr && (!diag || v <= r)) Cf[(long long)v * a.ldr + r] = out[row * 65 + col];
             }
-            if (RECIP) {
+            // the mirror (diagonal tiles always: their lower half is read by the update of a symmetric model)
+            if (RECIP && (diag || !a.no_mirror)) {
                 for (int e = tid; e < 128 * 64; e += TC_THREADS) {
                     const int rr = e >> 7, vv = e & 127, v = v0 + vv, r = rp + rr;
                     if (v < a.nv && r < a.nr && (!diag || v < r)) Cf[(long long)r * a.ldr + v] = out[vv * 65 + rr];

@@ -289,14 +289,17 @@ __device__ __forceinline__ void pass_compute(float2 (&a)[FFT_P], int t, const fl
             const float4 v1 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 1 * NS + k0));
             float4 v4 = v1;
             if constexpr (R == 8) v4 = __ldg(reinterpret_cast<const float4 *>(tw + TWOFF + 4 * NS + k0));
-            float2 w0[R], w1[R];
-            twiddle_powers<R>(make_float2(v1.x, v1.y), make_float2(v4.x, v4.y), w0);
-            twiddle_powers<R>(make_float2(v1.z, v1.w), make_float2(v4.z, v4.w), w1);
+            // one butterfly's powers at a time: half the twiddle registers live at once
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 &x0 = a[(2 * qq) * R + r], &x1 = a[(2 * qq + 1) * R + r];
-                x0 = INV ? cmulc(x0, w0[r]) : cmul(x0, w0[r]);
-                x1 = INV ? cmulc(x1, w1[r]) : cmul(x1, w1[r]);
+            for (int e = 0; e < 2; ++e) {
+                float2 w[R];
+                twiddle_powers<R>(e ? make_float2(v1.z, v1.w) : make_float2(v1.x, v1.y),
+                                  e ? make_float2(v4.z, v4.w) : make_float2(v4.x, v4.y), w);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 &x = a[(2 * qq + e) * R + r];
+                    x = INV ? cmulc(x, w[r]) : cmul(x, w[r]);
+                }
             }
         }
         dftR<R, INV>(&a[(2 * qq) * R]);
@@ -470,9 +473,10 @@ __device__ __forceinline__ void fwd_last_real(float2 (&a)[FFT_P], float2 *buf, i
         }
         dftR<R, false>(A);
         dftR<R, false>(B);
-        // X[k] = e - i w_N^k d, e = (Z[k] + conj Z[M-k]) / 2, d = (Z[k] - conj Z[M-k]) / 2
+        // X[k] = e - i w_N^k d, e = (Z[k] + conj Z[M-k]) / 2, d = (Z[k] - conj Z[M-k]) / 2; each bin goes to
+        // its slot as soon as it is formed (every load of this pass precedes the team sync above), so A
+        // and B are read-only here and no output array is held in registers
         const float2 wn = __ldg(twN + u);   // w_N^u
-        float2 xa[R], xb[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float2 za = A[r], zma = u ? B[R - 1 - r] : A[(R - r) % R];
@@ -481,16 +485,11 @@ __device__ __forceinline__ void fwd_last_real(float2 (&a)[FFT_P], float2 *buf, i
             const float2 wkb = u ? cmul(root32(16 * (r + 1) / R), cconj(wn)) : root32(8 / R + 16 * r / R);
             const float2 pa = cmul(wka, cscale(csub(za, cconj(zma)), 0.5f));
             const float2 pb = cmul(wkb, cscale(csub(zb, cconj(zmb)), 0.5f));
-            xa[r] = cadd(cscale(cadd(za, cconj(zma)), 0.5f), mul_mi<false>(pa));
-            xb[r] = cadd(cscale(cadd(zb, cconj(zmb)), 0.5f), mul_mi<false>(pb));
-        }
-        if (u == 0) {   // slot 0 packs X[0] and X[M] = Re Z[0] - Im Z[0]
-            xa[0] = make_float2(xa[0].x, A[0].x - A[0].y);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            buf[padi(ja[q] + r * S)] = xa[r];
-            buf[padi(jb[q] + r * S)] = xb[r];
+            float2 xa = cadd(cscale(cadd(za, cconj(zma)), 0.5f), mul_mi<false>(pa));
+            const float2 xb = cadd(cscale(cadd(zb, cconj(zmb)), 0.5f), mul_mi<false>(pb));
+            if (r == 0 && u == 0) xa = make_float2(xa.x, A[0].x - A[0].y);   // slot 0: X[0], X[M] = Re Z[0] - Im Z[0]
+            buf[padi(ja[q] + r * S)] = xa;
+            buf[padi(jb[q] + r * S)] = xb;
         }
     }
     team_sync<T>();
@@ -572,6 +571,17 @@ template <int M, int V>
 __device__ __forceinline__ void irfft_smem_to_regs(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
                                                    const float2 *__restrict__ twN) {
     inv_first_real<M, V>(a, buf, t, twN);
+    passes_from<M, true, 1, fft_npass(M), V>(a, buf, t, tw);
+}
+
+// The same with `mid()` run after the first pass: a caller that needs time-domain inputs after the
+// transform issues their loads there, so they are not held in registers through the real
+// pre-processing (the pass with the most live values) but still overlap the remaining passes.
+template <int M, int V, class F>
+__device__ __forceinline__ void irfft_smem_to_regs_mid(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
+                                                       const float2 *__restrict__ twN, F &&mid) {
+    inv_first_real<M, V>(a, buf, t, twN);
+    mid();
     passes_from<M, true, 1, fft_npass(M), V>(a, buf, t, tw);
 }
 

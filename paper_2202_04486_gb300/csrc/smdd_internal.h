@@ -21,6 +21,9 @@ struct TraceGrid {
     int ni, nj, ti_log2;
     long long tsi, tsj;
     long long ssi, ssj, ssf;
+    // 1: only the tiles on or above the block diagonal of a square grid (ni == nj, CTAs of TR traces along
+    // i): tile (bi, j) for bi >= j / TR, bi fastest (a symmetric model, see sym_tile_to_full)
+    int sym = 0;
 };
 
 struct FftArgs {
@@ -68,6 +71,9 @@ struct GemmArgs {
     int *status;
     int nf_active;           // band limit: bins f >= nf_active (when > 0) get zero products
     long long wait_probe;    // tensor-core kernels: > 0 = failure-path check (mdc_plan_set_wait_probe), cycles
+    int no_mirror;           // adjoint with reciprocity: skip the mirrored copy of the off-diagonal tiles (the
+                             // update of a symmetric model reads the upper tiles and the diagonal ones only;
+                             // a diagonal tile still mirrors its upper half, so it stays exactly symmetric)
 };
 
 // Zero the output tile [r0, r0+nrows) x [c0, c0+ncols) of a CTA whose frequency bin lies above the
@@ -90,6 +96,17 @@ struct WorkQueue {
     int n, total;
     unsigned int *counter;
 };
+
+// Symmetric model: X^[f][v][r] <- X^[f][r][v] for every r < TR floor(v / TR) (the part of the spectra below
+// the TR-block diagonal, which the update of a symmetric model leaves unwritten); n = nr = nv
+cudaError_t launch_mirror_lower(float2 *spec, int n, int ld, long long ssf, int nf, int TR, cudaStream_t st);
+// Number of tiles of the upper enumeration of a square grid of n x n traces with TR traces per CTA along
+// i: row j holds the tiles bi = j / TR .. ceil(n / TR) - 1.
+__host__ __device__ inline long long sym_tiles(int n, int TR) {
+    const long long nbi = (n + TR - 1) / TR, full = n / TR, rem = n % TR;
+    // groups g < full of TR rows with nbi - g tiles each, then rem rows of nbi - full tiles
+    return (long long)TR * (full * nbi - full * (full - 1) / 2) + rem * (nbi - full);
+}
 
 // FFT lengths of the trace kernels: powers of two 64 .. 8192 and 3072 (api.cu)
 bool nfft_supported(int nfft);

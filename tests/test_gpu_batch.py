@@ -250,15 +250,18 @@ def test_batched_epochs_equal_separate_steps_and_oracle():
         D, U_obs, perm, alpha, X0 = _member_data(k, shape, n_perm)
         plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb)
         steps = oracle.steps_per_epoch(ns, nb)
+        # the reciprocity member starts symmetric: its update runs on the upper triangle (SMDD_SYMMETRIC)
         m = dict(plan=plan, X=_cuda(X0), U_obs=_cuda(U_obs), perm=_cuda(perm, torch.int32), nb=nb, alpha=alpha,
-                 flags=binding.SMDD_RECIPROCITY if recip else 0,
+                 flags=(binding.SMDD_RECIPROCITY | binding.SMDD_SYMMETRIC) if recip else 0,
                  loss=torch.full((loss_rows, steps), -1.0, device="cuda", dtype=torch.float64))
         members.append(m)
         data.append((D, U_obs, perm, alpha, X0, recip, steps))
     batch = binding.MDCBatch(members, n_branches=3)
     assert batch.n_branches == 3
-    # kernels per epoch: begin + end, plus per member 5 launches in its first step and 4 in the others
-    assert batch.kernels_per_epoch == 2 + sum(4 * s + 1 for s in batch.steps)
+    # kernels per epoch: begin + end, plus per member 5 launches in its first step and 4 in the others, and
+    # for the symmetric member the copy of the spectra below the block diagonal after every update
+    n_sym = sum(s for s, shape in zip(batch.steps, MEMBERS) if shape[5])
+    assert batch.kernels_per_epoch == 2 + sum(4 * s + 1 for s in batch.steps) + n_sym
     batch.run(0, 2)
     batch.run(2, 1)
     torch.cuda.synchronize()
