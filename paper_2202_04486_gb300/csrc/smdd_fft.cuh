@@ -13,7 +13,7 @@
 // j + r M/R) to outputs (j - j%Ns) R + j%Ns + r Ns after the twiddles w_{Ns R}^{r (j%Ns)}.  Lengths
 // M = 2^k use radices 4 and 8; M = 1536 (FFT length 3072, the shortest 3-smooth length >= 2 nt - 1 for
 // nt in 1025 .. 1536) adds one radix-3 pass in the middle of the plan, which moves its values through
-// shared memory on its own (512 butterflies over the 96 threads of a team).  Between
+// shared memory on its own (512 butterflies over 64 of the 96 threads of a team).  Between
 // passes the values go through shared memory; the float2 index is XOR-swizzled within 16-element
 // groups so that both the contiguous reads and the strided writes of a half-warp hit distinct banks.
 // The first forward pass reads its inputs straight from registers (global loads or the output of a
@@ -350,39 +350,122 @@ __device__ __forceinline__ void pass_store(float2 *buf, int t, const float2 (&a)
 }
 
 // A radix-3 pass of span NS, shared memory to shared memory (never the first or last pass of a plan, so
-// no register hand-over): butterfly j = t + T q (q < ceil(M / 3T), the last round partial) reads
-// j + r M/3, applies w_{3 NS}^{r (j % NS)} (table rows 1 and 2), transforms and stores at
-// (j - j % NS) 3 + j % NS + r NS.  Team syncs between the loads and the stores and at the end.
+// no register hand-over): butterfly j reads j + r M/3, applies w_{3 NS}^{r (j % NS)} (table rows 1 and 2),
+// transforms and stores at (j - j % NS) 3 + j % NS + r NS.  Team syncs between the loads and the stores
+// and at the end.
+//
+// The M/3 butterflies go to the TA = pass3_threads(M) first threads of the team, j = t + TA q (q < M/(3 TA)),
+// TA a multiple of 16 that divides M/3 and NS | TA: every thread then has the same count, j % NS = t % NS
+// for all its butterflies (one pair of twiddles per pass), and its shared-memory offsets are per-thread
+// bases plus compile-time constants.  (At M = 1536: 64 of the 96 threads, 8 butterflies each.)
+__host__ __device__ constexpr int pass3_threads(int M, int NS) {
+    int best = 0;
+    for (int ta = 16; ta <= M / FFT_P; ta += 16)
+        if ((M / 3) % ta == 0 && ta % NS == 0) best = ta;
+    return best;
+}
+
 template <int M, bool INV, int NS, int TWOFF>
 __device__ __forceinline__ void pass3_smem(float2 *buf, int t, const float2 *__restrict__ tw) {
-    constexpr int T = M / FFT_P, NBF = M / 3, NQ = (NBF + T - 1) / T;
-    float2 x[NQ][3];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int j = t + T * q;
-        if (j < NBF) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r) x[q][r] = buf[padi(j + r * NBF)];
-        }
-    }
-    team_sync<T>();
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int j = t + T * q;
-        if (j < NBF) {
-            const int k = j % NS;
+    constexpr int T = M / FFT_P, NBF = M / 3;
+    constexpr int TA = pass3_threads(M, NS);
+    if constexpr (TA > 0 && NS % 16 == 0) {
+        // spans that are multiples of 16: every offset below splits as padi(base) + padi(constant)
+        constexpr int NQ = NBF / TA;
+        if (t < TA) {
+            const int k = t % NS;
+            float2 w1 = make_float2(1.f, 0.f), w2 = w1;
             if constexpr (NS > 1) {
-                const float2 w1 = __ldg(tw + TWOFF + NS + k), w2 = __ldg(tw + TWOFF + 2 * NS + k);
-                x[q][1] = INV ? cmulc(x[q][1], w1) : cmul(x[q][1], w1);
-                x[q][2] = INV ? cmulc(x[q][2], w2) : cmul(x[q][2], w2);
+                w1 = __ldg(tw + TWOFF + NS + k);
+                w2 = __ldg(tw + TWOFF + 2 * NS + k);
             }
-            dft3<INV>(x[q][0], x[q][1], x[q][2]);
-            const int o = (j - k) * 3 + k;
+            const float2 *src = buf + padi(t);
+            float2 x[NQ][3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) buf[padi(o + r * NS)] = x[q][r];
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) x[q][r] = src[padi(TA * q + r * NBF)];
+            team_sync<T>();
+            float2 *dst = buf + padi((t - k) * 3 + k);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if constexpr (NS > 1) {
+                    x[q][1] = INV ? cmulc(x[q][1], w1) : cmul(x[q][1], w1);
+                    x[q][2] = INV ? cmulc(x[q][2], w2) : cmul(x[q][2], w2);
+                }
+                dft3<INV>(x[q][0], x[q][1], x[q][2]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) dst[padi(3 * TA * q + r * NS)] = x[q][r];
+            }
+        } else {
+            team_sync<T>();
         }
+        team_sync<T>();
+    } else if constexpr (TA > 0) {
+        // spans below 16 (NS | 16): the store offset (j - k) 3 + k + r NS has three per-thread bases
+        constexpr int NQ = NBF / TA;
+        if (t < TA) {
+            const int k = t % NS;
+            float2 w1 = make_float2(1.f, 0.f), w2 = w1;
+            if constexpr (NS > 1) {
+                w1 = __ldg(tw + TWOFF + NS + k);
+                w2 = __ldg(tw + TWOFF + 2 * NS + k);
+            }
+            const float2 *src = buf + padi(t);
+            float2 x[NQ][3];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) x[q][r] = src[padi(TA * q + r * NBF)];
+            team_sync<T>();
+            const int o = (t - k) * 3 + k;   // 3 TA q is a multiple of 16: padi(o + r NS + 3 TA q) = padi(o + r NS) + padi(3 TA q)
+            float2 *d0 = buf + padi(o), *d1 = buf + padi(o + NS), *d2 = buf + padi(o + 2 * NS);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if constexpr (NS > 1) {
+                    x[q][1] = INV ? cmulc(x[q][1], w1) : cmul(x[q][1], w1);
+                    x[q][2] = INV ? cmulc(x[q][2], w2) : cmul(x[q][2], w2);
+                }
+                dft3<INV>(x[q][0], x[q][1], x[q][2]);
+                d0[padi(3 * TA * q)] = x[q][0];
+                d1[padi(3 * TA * q)] = x[q][1];
+                d2[padi(3 * TA * q)] = x[q][2];
+            }
+        } else {
+            team_sync<T>();
+        }
+        team_sync<T>();
+    } else {
+        // general case: butterfly j = t + T q, the last round partial
+        constexpr int NQ = (NBF + T - 1) / T;
+        float2 x[NQ][3];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = t + T * q;
+            if (j < NBF) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) x[q][r] = buf[padi(j + r * NBF)];
+            }
+        }
+        team_sync<T>();
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = t + T * q;
+            if (j < NBF) {
+                const int k = j % NS;
+                if constexpr (NS > 1) {
+                    const float2 w1 = __ldg(tw + TWOFF + NS + k), w2 = __ldg(tw + TWOFF + 2 * NS + k);
+                    x[q][1] = INV ? cmulc(x[q][1], w1) : cmul(x[q][1], w1);
+                    x[q][2] = INV ? cmulc(x[q][2], w2) : cmul(x[q][2], w2);
+                }
+                dft3<INV>(x[q][0], x[q][1], x[q][2]);
+                const int o = (j - k) * 3 + k;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) buf[padi(o + r * NS)] = x[q][r];
+            }
+        }
+        team_sync<T>();
     }
-    team_sync<T>();
 }
 
 template <int M, bool INV, int p, int PEND, int V>
@@ -577,12 +660,22 @@ __device__ __forceinline__ void irfft_smem_to_regs(float2 (&a)[FFT_P], float2 *b
 // The same with `mid()` run after the first pass: a caller that needs time-domain inputs after the
 // transform issues their loads there, so they are not held in registers through the real
 // pre-processing (the pass with the most live values) but still overlap the remaining passes.
+//
+// Where the second inverse pass is the radix-3 pass (the one that holds the most values at once), mid()
+// runs after it instead.
+template <int M, int V>
+__host__ __device__ constexpr int irfft_mid_pass() {
+    return (fft_npass(M) > 2 && ifft_radix(M, 1, V) == 3) ? 2 : 1;
+}
+
 template <int M, int V, class F>
 __device__ __forceinline__ void irfft_smem_to_regs_mid(float2 (&a)[FFT_P], float2 *buf, int t, const float2 *__restrict__ tw,
                                                        const float2 *__restrict__ twN, F &&mid) {
+    constexpr int MP = irfft_mid_pass<M, V>();
     inv_first_real<M, V>(a, buf, t, twN);
+    passes_from<M, true, 1, MP, V>(a, buf, t, tw);
     mid();
-    passes_from<M, true, 1, fft_npass(M), V>(a, buf, t, tw);
+    passes_from<M, true, MP, fft_npass(M), V>(a, buf, t, tw);
 }
 
 }  // namespace smdd
