@@ -70,6 +70,9 @@ struct mdc_plan_s {
     int *status = nullptr;
     int resid_blocks_max = 0;
     const float *xhat_for = nullptr;  // model pointer whose spectrum Xh holds (KEEP_XHAT)
+    int xhat_upper_tr = 0;            // > 0: Xh holds a symmetric model's spectra on and above the block
+                                      // diagonal of this many traces only (the lower part is read transposed
+                                      // by the tile forward product, or copied before another kernel reads it)
     bool profiling = false;
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
@@ -191,6 +194,7 @@ TraceGrid batch_grid(const mdc_plan_s *p, int nb) {
 }
 
 int rfft_model(mdc_plan_s *p, const float *X, cudaStream_t st) {
+    p->xhat_upper_tr = 0;   // every bin of every trace
     FftArgs a = base_fft(p);
     a.g = model_grid(p, p->nv);
     a.tin = X;
@@ -214,6 +218,20 @@ int gemm_forward(mdc_plan_s *p, const int32_t *idx, int nb, cudaStream_t st) {
     g.status = p->status;
     g.nf_active = p->nf_active;
     g.wait_probe = p->wait_probe;
+    if (p->xhat_upper_tr > 0) {
+        // the spectra below the block diagonal of a symmetric model: read transposed by the tile kernel,
+        // else copied into place first
+        if (p->gemm_fwd == MDC_GEMM_TC) {
+            g.sym_tr = p->xhat_upper_tr;
+        } else {
+            const int tr = p->xhat_upper_tr;
+            p->xhat_upper_tr = 0;
+            const int rc = launch_stage(p, ST_GEMM_FWD, st, [&] {
+                return launch_mirror_lower(p->Xh, p->nv, p->ldr, (long long)p->nv * p->ldr, p->nf, tr, st);
+            });
+            if (rc) return rc;
+        }
+    }
     if (p->gemm_fwd == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_FWD, st, [&] { return launch_tc_fwd(g, p->nf, st); });
     if (p->gemm_fwd == MDC_GEMM_TC_STREAM && p->xh_map_ok)
@@ -669,14 +687,17 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
         a.eps = adam.eps;
         a.c1 = adam.c1;
         a.c2 = adam.c2;
-        // a symmetric model's spectra below the block diagonal are copies of the ones above it
+        // a symmetric model's spectra below the block diagonal are copies of the ones above it: the tile
+        // forward product of the next step reads them transposed, any other kernel needs the copy
+        const bool mirror = keep && sym && p->gemm_fwd != MDC_GEMM_TC;
         if ((rc = launch_stage(p, ST_UPDATE, st, [&] {
                  const cudaError_t e = launch_update(p->M, keep, a, st);
-                 if (e != cudaSuccess || !(keep && sym)) return e;
+                 if (e != cudaSuccess || !mirror) return e;
                  return launch_mirror_lower(p->Xh, p->nv, p->ldr, (long long)p->nv * p->ldr, p->nf, tr_upd, st);
              })))
             return rc;
         if (keep) p->xhat_for = X;
+        p->xhat_upper_tr = (keep && sym && !mirror) ? tr_upd : 0;
     }
     return MDC_OK;
 }

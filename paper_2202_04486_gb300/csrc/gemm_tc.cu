@@ -51,6 +51,20 @@ __device__ __forceinline__ void load8(const float2 *row, int k, int n, float2 (&
     }
 }
 
+// Row v of a symmetric model's spectra, elements k .. k+8 (zero past n), when only the part on and above
+// the TR-block diagonal is stored: element r < lo = TR floor(v / TR) is read at (r, v) (column v of row r).
+__device__ __forceinline__ void load8_sym(const float2 *Af, long long ld, int v, int k, int n, int lo, float2 (&z)[8]) {
+    if (k >= lo) {
+        load8(Af + (long long)v * ld, k, n, z);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = k + i;
+            z[i] = r < n ? __ldg(r >= lo ? Af + (long long)v * ld + r : Af + (long long)r * ld + v) : make_float2(0.f, 0.f);
+        }
+    }
+}
+
 // store one 16-byte chunk of each plane; planes are `pstride` bytes apart
 __device__ __forceinline__ void store_planes(uint8_t *base, int off, int pstride, const Chunk4 &c) {
     *reinterpret_cast<uint4 *>(base + off) = c.rh;
@@ -155,7 +169,10 @@ __device__ __forceinline__ void tc_fwd_body(const GemmArgs &a, int bx, int by, i
 #pragma unroll
             for (int i = 0; i < UA; ++i) {
                 const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7, v = v0 + row;
-                load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z[i]);
+                if (a.sym_tr > 0 && v < a.nv)
+                    load8_sym(Af, a.ldr, v, kc * 64 + 8 * c, a.nr, a.sym_tr * (v / a.sym_tr), z[i]);
+                else
+                    load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z[i]);
             }
             // stage s is free again once the MMAs of chunk kc - NSTAGE (the previous use of bars[s]) are done
             if (kc >= NSTAGE && !mbar_wait_bounded(&bars[s], ((kc - NSTAGE) / NSTAGE) & 1)) fail = 1;

@@ -71,6 +71,9 @@ struct GemmArgs {
     int *status;
     int nf_active;           // band limit: bins f >= nf_active (when > 0) get zero products
     long long wait_probe;    // tensor-core kernels: > 0 = failure-path check (mdc_plan_set_wait_probe), cycles
+    int sym_tr;              // forward: > 0 when A holds a symmetric model's spectra only on and above the
+                             // sym_tr-block diagonal: element (v, r) with r < sym_tr floor(v / sym_tr) is read
+                             // at (r, v)
     int no_mirror;           // adjoint with reciprocity: skip the mirrored copy of the off-diagonal tiles (the
                              // update of a symmetric model reads the upper tiles and the diagonal ones only;
                              // a diagonal tile still mirrors its upper half, so it stays exactly symmetric)

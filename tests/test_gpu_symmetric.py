@@ -118,3 +118,27 @@ def test_symmetric_flag_ignored_without_reciprocity_and_with_momentum():
                              binding.SMDD_RECIPROCITY | binding.SMDD_SYMMETRIC | binding.SMDD_NESTEROV,
                              V=torch.zeros_like(Xb), mu=0.5)
     plan.close()
+
+
+def test_lower_spectra_read_transposed_or_copied_when_the_kernel_changes():
+    """With the tile forward product the spectra below the block diagonal are not copied: the next
+    forward product reads them transposed.  A plan switched to another forward kernel between two steps
+    copies them into place first.  Either way the steps equal the steps without the flag bit for bit."""
+    nt, n, ns, nb = 512, 70, 40, 16
+    D, X, U = _problem(nt, n, ns, seed=21)
+    rng = np.random.default_rng(9)
+    batches = [rng.permutation(ns)[:nb].astype(np.int32) for _ in range(4)]
+    kernels = [binding.MDC_GEMM_TC, binding.MDC_GEMM_TC, binding.MDC_GEMM_SIMT, binding.MDC_GEMM_TC]
+    outs = []
+    for sym in (False, True):
+        plan = binding.MDCPlan(_cuda(D), n, nb_max=nb, precision=binding.MDC_PREC_BF16X3)
+        alpha = 0.3 / plan.sigma2_max(30)
+        Xg, Ug = _cuda(X), _cuda(U)
+        for k, (b, fwd) in enumerate(zip(batches, kernels)):
+            plan.set_config(fft_variant=0, fft_prefetch=0, gemm_fwd=fwd, gemm_adj=binding.MDC_GEMM_TC)
+            fl = binding.SMDD_RECIPROCITY | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+            plan.step(Xg, Ug, _cuda(b, torch.int32), alpha, fl | (binding.SMDD_SYMMETRIC if sym else 0))
+        assert plan.sync_status() == binding.MDC_OK
+        outs.append(Xg.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
