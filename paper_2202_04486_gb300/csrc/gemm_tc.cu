@@ -107,7 +107,7 @@ struct TcFwd {
 // Tile (bx, by, bz) = (row block of 128 virtual sources, batch block of NB, bin f).  Q: a work-queue
 // item of a persistent CTA, which owns its TMEM (tmem_q) for all its items; the barriers are
 // invalidated at the end of the item so that the next one can initialise them again.
-template <int NB, int NSTAGE, bool Q>
+template <int NB, int NSTAGE, bool Q, bool SYM = false>
 __device__ __forceinline__ void tc_fwd_body(const GemmArgs &a, int bx, int by, int bz, uint32_t tmem_q) {
     using G = TcFwd<NB, NSTAGE>;
     extern __shared__ uint8_t tc_raw[];
@@ -169,7 +169,7 @@ __device__ __forceinline__ void tc_fwd_body(const GemmArgs &a, int bx, int by, i
 #pragma unroll
             for (int i = 0; i < UA; ++i) {
                 const int u = tid + i * TC_THREADS, row = u >> 3, c = u & 7, v = v0 + row;
-                if (a.sym_tr > 0 && v < a.nv)
+                if (SYM && v < a.nv)
                     load8_sym(Af, a.ldr, v, kc * 64 + 8 * c, a.nr, a.sym_tr * (v / a.sym_tr), z[i]);
                 else
                     load8(v < a.nv ? Af + (long long)v * a.ldr : nullptr, kc * 64 + 8 * c, a.nr, z[i]);
@@ -251,9 +251,10 @@ __device__ __forceinline__ void tc_fwd_body(const GemmArgs &a, int bx, int by, i
     }
 }
 
-template <int NB, int NSTAGE>
+// SYM: the model spectra hold a symmetric model on and above the a.sym_tr-block diagonal only (load8_sym)
+template <int NB, int NSTAGE, bool SYM = false>
 __global__ void __launch_bounds__(TC_THREADS, NSTAGE == 1 ? 2 : 1) k_tc_fwd(GemmArgs a) {
-    tc_fwd_body<NB, NSTAGE, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, 0);
+    tc_fwd_body<NB, NSTAGE, false, SYM>(a, blockIdx.x, blockIdx.y, blockIdx.z, 0);
 }
 
 // work-queue form: persistent CTAs (TMEM allocated once) taking (problem, tile) items; tile t of a
@@ -821,6 +822,9 @@ cudaError_t tc_prepare() {
     if ((e = cudaFuncSetAttribute(k_tc_fwd<16, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd<32, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd<64, TC_FWD_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<16, TC_FWD_STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<32, TC_FWD_STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, TC_FWD_STAGES>::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_fwd<64, TC_FWD_STAGES, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, TC_FWD_STAGES>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<16>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<32>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<64>::SMEM))) return e;
@@ -838,6 +842,12 @@ cudaError_t tc_prepare() {
 cudaError_t launch_tc_fwd(const GemmArgs &a, int nf, cudaStream_t st) {
     const int gx = (a.nv + 127) / 128;
     constexpr int S = TC_FWD_STAGES;
+    if (a.sym_tr > 0) {
+        if (a.nb <= 16) k_tc_fwd<16, S, true><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16, S>::SMEM, st>>>(a);
+        else if (a.nb <= 32) k_tc_fwd<32, S, true><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32, S>::SMEM, st>>>(a);
+        else k_tc_fwd<64, S, true><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64, S>::SMEM, st>>>(a);
+        return cudaGetLastError();
+    }
     if (a.nb <= 16) k_tc_fwd<16, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<16, S>::SMEM, st>>>(a);
     else if (a.nb <= 32) k_tc_fwd<32, S><<<dim3(gx, 1, nf), TC_THREADS, TcFwd<32, S>::SMEM, st>>>(a);
     else k_tc_fwd<64, S><<<dim3(gx, (a.nb + 63) / 64, nf), TC_THREADS, TcFwd<64, S>::SMEM, st>>>(a);
