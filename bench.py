@@ -117,8 +117,10 @@ def kernel_work(stage, nt, nr, nv, nb, sym=False):
     nf = nf_of(nt)
     ff = fft_flops(nt)
     if stage == "update" and sym:
-        up, low = model_traces(nr, nv, True), nr * nv - model_traces(nr, nv, True)
-        return dict(bytes=(up + nr * nv) * nt * 4, flops=2 * ff * up, staged=2 * (up + low) * nf * 8, tensor=False)
+        # gradient spectra read and model spectra written on the distinct traces (the forward product reads the
+        # rest transposed)
+        up = model_traces(nr, nv, True)
+        return dict(bytes=(up + nr * nv) * nt * 4, flops=2 * ff * up, staged=2 * up * nf * 8, tensor=False)
     if stage == "update":      # inverse FFT of the gradient, update, FFT of the new model, per model trace
         return dict(bytes=2 * nv * nr * nt * 4, flops=2 * ff * nv * nr, staged=2 * nv * nr * nf * 8, tensor=False)
     if stage == "cgemm_fwd":   # products with the gathered kernel rows; model spectra in, batch spectra out
