@@ -61,6 +61,7 @@ struct mdc_plan_s {
     float2 *Dh = nullptr;        // [nf][ns][ldr]
     float2 *Xh = nullptr;        // [nf][nv][ldr]  model spectra, reused for gradient spectra
     float2 *Uh = nullptr;        // [nf][nv][ldb]  batch spectra (prediction, then residual)
+    uint8_t *adj_img = nullptr;  // split-BF16 plans: operand images of the adjoint products (null: not held)
     float2 *tw = nullptr;        // twiddle tables of the FFT variants: 0 at 0, 1 at tw1_off, 2 at tw2_off
     int tw1_off = 0, tw2_off = 0;
     float2 *twN = nullptr;       // [M+1]
@@ -259,6 +260,13 @@ int gemm_adjoint(mdc_plan_s *p, const int32_t *idx, int nb, bool recip, cudaStre
     g.no_mirror = (recip && no_mirror) ? 1 : 0;
     if (p->gemm_adj == MDC_GEMM_TC)
         return launch_stage(p, ST_GEMM_ADJ, st, [&] {
+            // the operand images of this step's residual spectra and batch rows, then the products from them
+            if (p->adj_img && tc_adj_image_bytes(p->nv, p->nr, nb, p->nf) > 0) {
+                const cudaError_t e = launch_tc_adj_images(g, p->adj_img, p->nf, st);
+                if (e != cudaSuccess) return e;
+                g.img = p->adj_img;
+                g.img_nkc = (nb + 31) / 32;
+            }
             return launch_tc_adj(g, recip, p->nf, st, (SMDD_TC_ADJ_TMA && p->xh_map_ok) ? p->xh_map : nullptr);
         });
     if (p->gemm_adj == MDC_GEMM_GEMV && gemv_supported(p->nv) && !recip && p->nf_active == 0 && nb <= 1024)
@@ -414,6 +422,15 @@ int mdc_plan_create(mdc_plan_t *out, int nt, int nr, int nv, int ns, int nb_max,
         mdc_plan_destroy(p);
         return MDC_ERR_OOM;
     }
+    // split-BF16 plans: operand images for the adjoint products of batches up to 64 (the products split their
+    // operands themselves where these do not fit)
+    if (precision == MDC_PREC_BF16X3) {
+        const size_t bytes = tc_adj_image_bytes(nv, nr, nb_max, nf);
+        if (bytes > 0 && cudaMalloc(&p->adj_img, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p->adj_img = nullptr;
+        }
+    }
     // per-pass twiddle tables in double precision, rounded once to float
     const double pi = 3.14159265358979323846;
     std::vector<float2> tw, tw1;
@@ -509,6 +526,7 @@ int mdc_plan_destroy(mdc_plan_t p) {
     cudaFree(p->Dh);
     cudaFree(p->Xh);
     cudaFree(p->Uh);
+    cudaFree(p->adj_img);
     cudaFree(p->tw);
     cudaFree(p->twN);
     cudaFree(p->partials);

@@ -317,8 +317,75 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Tile bx of bin by (the upper-triangular enumeration with reciprocity); Q as for tc_fwd_body.
-template <bool RECIP, bool Q, bool TMA = false>
+// Operand images: per bin f and K chunk kc, for every 128-wide block of the virtual sources (R, from the
+// residual spectra) and of the receivers (D, from the conjugated kernel rows of the batch), the four
+// split-BF16 planes exactly as the tile kernel's shared memory holds them (MN-major, 128-byte swizzle):
+// R image of block b at [f][kc][b], D image of block b at [f][kc][tiles_v + b], TC_ADJ_IMG bytes each.
+// The adjoint then copies two images per half instead of loading, transposing and splitting its operands
+// (every operand block serves a whole row or column of output tiles).
+constexpr int TC_ADJ_IMG = 4 * TcAdj::PLANE;
+
+__global__ void __launch_bounds__(TC_THREADS) k_tc_adj_images(GemmArgs a, uint8_t *img) {
+    using G = TcAdj;
+    constexpr int KC = G::KC;
+    extern __shared__ __align__(16) float2 stg[];   // residual staging [128][SLD]
+    __shared__ int sidx[KC];
+    const int blk = blockIdx.x, kc = blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
+    const int k0 = kc * KC, kn = min(KC, a.nb - k0);
+    const int nbl = a.tiles_v + a.tiles_r;
+    uint8_t *dst = img + (((long long)f * a.img_nkc + kc) * nbl + blk) * (long long)TC_ADJ_IMG;
+    if (blk < a.tiles_v) {
+        // R image: residual rows cr .. cr + 127 (b contiguous), staged, then transposed and split
+        const int cr = blk * 128;
+        const float2 *Rf = a.A + (long long)f * a.sAf;
+        for (int u = tid; u < 128 * (KC / 2); u += TC_THREADS) {
+            const int row = u / (KC / 2), pr = u % (KC / 2), k = k0 + 2 * pr, rr = cr + row;
+            int bytes = 0;
+            const float2 *src = Rf;
+            if (rr < a.nv && k < a.nb) {
+                bytes = (k + 1 < a.nb) ? 16 : 8;
+                src = Rf + (long long)rr * a.ldb + k;
+            }
+            cp_async16_zfill(stg + row * G::SLD + 2 * pr, src, bytes);
+        }
+        cp_async_commit_wait_all();
+        __syncthreads();
+        for (int u = tid; u < KC * 16; u += TC_THREADS) {
+            const int k = u % KC, ch = u / KC, at = ch >> 3, c = ch & 7;
+            float2 z[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) z[j] = stg[(64 * at + 8 * c + j) * G::SLD + k];
+            store_planes(dst, at * (KC * 128) + k * 128 + ((c ^ (k & 7)) << 4), G::PLANE, split8(z, false));
+        }
+    } else {
+        // D image: conjugated kernel rows of the batch entries k0 .. k0 + 31, receivers cd .. cd + 127
+        const int cd = (blk - a.tiles_v) * 128;
+        if (tid < KC) {
+            int sr = -1;
+            if (tid < kn) {
+                sr = a.idx[k0 + tid];
+                if (sr < 0 || sr >= a.ns) {
+                    atomicOr(a.status, 1);
+                    sr = -1;
+                }
+            }
+            sidx[tid] = sr;
+        }
+        __syncthreads();
+        const float2 *Df = a.Dh + (long long)f * a.sDf;
+        for (int u = tid; u < KC * 16; u += TC_THREADS) {
+            const int k = u >> 4, ch = u & 15, at = ch >> 3, c = ch & 7;
+            const int srow = sidx[k];
+            float2 z[8];
+            load8(srow >= 0 ? Df + (long long)srow * a.ldr : nullptr, cd + 64 * at + 8 * c, a.nr, z);
+            store_planes(dst, at * (KC * 128) + k * 128 + ((c ^ (k & 7)) << 4), G::PLANE, split8(z, true));
+        }
+    }
+}
+
+// Tile bx of bin by (the upper-triangular enumeration with reciprocity); Q as for tc_fwd_body.  IMG: the
+// operands come from the images of k_tc_adj_images (a.img).
+template <bool RECIP, bool Q, bool TMA = false, bool IMG = false>
 __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, uint32_t tmem_q,
                                             const CUtensorMap *tmap = nullptr) {
     using G = TcAdj;
@@ -352,13 +419,15 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
     const float2 *Rf = a.A + (long long)f * a.sAf;
     const float2 *Df = a.Dh + (long long)f * a.sDf;
 
-    for (int b = tid; b < a.nb; b += TC_THREADS) {
-        int s = a.idx[b];
-        if (s < 0 || s >= a.ns) {
-            atomicOr(a.status, 1);
-            s = -1;
+    if constexpr (!IMG) {
+        for (int b = tid; b < a.nb; b += TC_THREADS) {
+            int s = a.idx[b];
+            if (s < 0 || s >= a.ns) {
+                atomicOr(a.status, 1);
+                s = -1;
+            }
+            sidx[b] = s;
         }
-        sidx[b] = s;
     }
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -389,6 +458,26 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
         const int kc = job / nhalf, half = job % nhalf;
         const int k0 = kc * KC;
         const int kn = min(KC, a.nb - k0), kpad = (kn + 15) & ~15;
+        if constexpr (IMG) {
+            // the previous products must be done reading the planes
+            if (job > 0) {
+                if (!mbar_wait_bounded(&bar, phase & 1)) fail = 1;
+                ++phase;
+            }
+            tc_fence_after();
+            // half 0: A' = R image of the row block, B' = D image of the column block; half 1 the other way
+            const int nbl = a.tiles_v + a.tiles_r;
+            const uint8_t *base = a.img + ((long long)f * a.img_nkc + kc) * nbl * (long long)TC_ADJ_IMG;
+            const uint8_t *ia = base + (long long)(half ? a.tiles_v + vb : vb) * TC_ADJ_IMG;
+            const uint8_t *ib = base + (long long)(half ? rb : a.tiles_v + rb) * TC_ADJ_IMG;
+            for (int u = tid; u < TC_ADJ_IMG / 16; u += TC_THREADS) {
+                cp_async16_zfill(sA + 16 * u, ia + 16 * u, 16);
+                cp_async16_zfill(sB + 16 * u, ib + 16 * u, 16);
+            }
+            cp_async_commit_wait_all();
+            fence_async_smem();
+            __syncthreads();
+        } else {
         const int cr = half ? r0 : v0, ncr = half ? a.nr : a.nv;   // residual rows of this half
         const int cd = half ? v0 : r0, ncd = half ? a.nv : a.nr;   // kernel-row columns of this half
         // residual rows -> staging (cp.async, zero-filled past the matrix); the staging tile was
@@ -435,6 +524,7 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
         }
         fence_async_smem();
         __syncthreads();
+        }
         if (fail) break;
         if (tid == 0) {
             tc_fence_after();
@@ -555,15 +645,16 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
     }
 }
 
-template <bool RECIP>
+template <bool RECIP, bool IMG = false>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
-    tc_adj_body<RECIP, false>(a, blockIdx.x, blockIdx.y, 0);
+    tc_adj_body<RECIP, false, false, IMG>(a, blockIdx.x, blockIdx.y, 0);
 }
 
 // the adjoint without reciprocity with its tile written by the tensor memory accelerator (tmap: the
 // tensor map of the gradient spectra, i.e. of the model-spectra buffer, FP32 [nf][nv][2 nr])
+template <bool IMG = false>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj_tma(GemmArgs a, const __grid_constant__ CUtensorMap tmap) {
-    tc_adj_body<false, false, true>(a, blockIdx.x, blockIdx.y, 0, &tmap);
+    tc_adj_body<false, false, true, IMG>(a, blockIdx.x, blockIdx.y, 0, &tmap);
 }
 
 // work-queue form: tile t of a problem is (bx, by) = (t % tiles, t / tiles) with tiles the output tiles
@@ -830,7 +921,10 @@ cudaError_t tc_prepare() {
     if ((e = cudaFuncSetAttribute(k_tc_fwd_stream<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdS<64>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
-    if ((e = cudaFuncSetAttribute(k_tc_adj_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, 1>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, 1>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, 1>::SMEM))) return e;
@@ -927,15 +1021,35 @@ cudaError_t launch_tc_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t s
     GemmArgs a = a0;
     a.tiles_v = (a.nv + 127) / 128;
     a.tiles_r = (a.nr + 127) / 128;
+    const bool img = a.img != nullptr;
     if (recip) {
-        k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+        if (img) k_tc_adj<true, true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+        else k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
     } else if (map) {
         CUtensorMap tmap;
         memcpy(&tmap, map, sizeof(tmap));
-        k_tc_adj_tma<<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
+        if (img) k_tc_adj_tma<true><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
+        else k_tc_adj_tma<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
     } else {
-        k_tc_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+        if (img) k_tc_adj<false, true><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
+        else k_tc_adj<false><<<dim3(a.tiles_v * a.tiles_r, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+size_t tc_adj_image_bytes(int nv, int nr, int nb, int nf) {
+    const int nkc = (nb + TcAdj::KC - 1) / TcAdj::KC;
+    if (nkc < 1 || nkc > 2) return 0;
+    return (size_t)nf * nkc * (size_t)((nv + 127) / 128 + (nr + 127) / 128) * TC_ADJ_IMG;
+}
+
+cudaError_t launch_tc_adj_images(const GemmArgs &a0, uint8_t *img, int nf, cudaStream_t st) {
+    GemmArgs a = a0;
+    a.tiles_v = (a.nv + 127) / 128;
+    a.tiles_r = (a.nr + 127) / 128;
+    a.img_nkc = (a.nb + TcAdj::KC - 1) / TcAdj::KC;
+    const int nfa = (a.nf_active > 0 && a.nf_active < nf) ? a.nf_active : nf;   // bins above a band limit are zero
+    k_tc_adj_images<<<dim3(a.tiles_v + a.tiles_r, a.img_nkc, nfa), TC_THREADS, TcAdj::STAGE, st>>>(a, img);
     return cudaGetLastError();
 }
 

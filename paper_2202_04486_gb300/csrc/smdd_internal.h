@@ -74,6 +74,8 @@ struct GemmArgs {
     int sym_tr;              // forward: > 0 when A holds a symmetric model's spectra only on and above the
                              // sym_tr-block diagonal: element (v, r) with r < sym_tr floor(v / sym_tr) is read
                              // at (r, v)
+    const uint8_t *img;      // adjoint, split-BF16 tile kernel: the operand images of k_tc_adj_images (or null:
+    int img_nkc;             // the kernel splits its operands itself), their K chunks (32 batch entries each)
     int no_mirror;           // adjoint with reciprocity: skip the mirrored copy of the off-diagonal tiles (the
                              // update of a symmetric model reads the upper tiles and the diagonal ones only;
                              // a diagonal tile still mirrors its upper half, so it stays exactly symmetric)
@@ -169,6 +171,10 @@ cudaError_t launch_tc_fwd_stream(const GemmArgs &a, const void *map, int nf, cud
 // map (or null): the 128-byte tensor map of the output (tc_encode_fwd_map of the model-spectra buffer):
 // the tile without reciprocity is then written by the tensor memory accelerator
 cudaError_t launch_tc_adj(const GemmArgs &a, bool recip, int nf, cudaStream_t st, const void *map = nullptr);
+// Operand images of the split-BF16 adjoint (bytes for a problem; 0 where the batch needs more than two K
+// chunks), and their construction for one step (residual spectra and gathered kernel rows of a.idx).
+size_t tc_adj_image_bytes(int nv, int nr, int nb, int nf);
+cudaError_t launch_tc_adj_images(const GemmArgs &a, uint8_t *img, int nf, cudaStream_t st);
 // work-queue forms of the tensor-core tile products (persistent CTAs, TMEM allocated once per CTA);
 // tile counts per problem: tc_fwd_tiles (NB = tc_fwd_queue_nb(nb) for every member of a launch),
 // tc_adj_tiles (which also sets the record's tiles_v / tiles_r)

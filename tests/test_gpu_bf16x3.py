@@ -146,3 +146,47 @@ def test_streamed_forward_reports_index_errors():
     with pytest.raises(binding.MDCError) as e:
         fp32.set_config(gemm_fwd=binding.MDC_GEMM_TC_STREAM)
     assert e.value.status == binding.MDC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [(100, 37, 29, 41, 5), (64, 150, 140, 160, 24), (257, 130, 130, 70, 40),
+                                   (64, 140, 140, 80, 64)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("recip", [False, True])
+def test_adjoint_operand_images_equal_inline_split(shape, recip):
+    """The adjoint products from the per-step operand images (plans for batches up to 64) against the
+    products that load and split their operands themselves (a plan for larger batches): the same split and
+    the same MMAs in the same order, so bit-identical gradients and steps; ragged blocks, one and two K
+    chunks, an out-of-range source index reported."""
+    nt, nr, nv, ns, nb = shape
+    if recip:
+        nv = nr
+    seed = sum(shape) + recip
+    D = _f32(synth.random_traces((ns, nr, nt), seed))
+    R = _f32(synth.random_traces((nb, nv, nt), seed + 1))
+    X = _f32(oracle.reciprocity(synth.random_traces((nv, nr, nt), seed + 2))) if recip else \
+        _f32(synth.random_traces((nv, nr, nt), seed + 2))
+    U = _f32(synth.random_traces((ns, nv, nt), seed + 3))
+    idx = synth.random_indices(ns, nb, seed + 4)
+    ti = _cuda(idx, torch.int32)
+    out = []
+    for nb_max in (nb, 65):   # images held / not held
+        plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb_max, precision=binding.MDC_PREC_BF16X3)
+        plan.set_config(gemm_fwd=binding.MDC_GEMM_TC, gemm_adj=binding.MDC_GEMM_TC)
+        G = plan.adjoint(_cuda(R), ti)
+        Xg = _cuda(X)
+        plan.step(Xg, _cuda(U), ti, 1e-3, binding.SMDD_RECIPROCITY if recip else 0)
+        assert plan.sync_status() == binding.MDC_OK
+        out.append((G.cpu().numpy(), Xg.cpu().numpy()))
+        plan.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    _check(out[0][0], oracle.mdc_adjoint(D, R, idx), "G")
+    # an out-of-range index is reported by the image construction; its batch entry contributes nothing
+    plan = binding.MDCPlan(_cuda(D), nv, nb_max=nb, precision=binding.MDC_PREC_BF16X3)
+    plan.set_config(gemm_adj=binding.MDC_GEMM_TC)
+    bad = idx.copy()
+    bad[0] = ns + 3
+    G = plan.adjoint(_cuda(R), _cuda(bad, torch.int32)).cpu().numpy()
+    assert plan.sync_status() == binding.MDC_ERR_INDEX_RANGE
+    keep = np.arange(1, nb)
+    _check(G, oracle.mdc_adjoint(D, R[keep], bad[keep]), "G without the bad entry")
+    plan.close()
