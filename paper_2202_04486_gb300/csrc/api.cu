@@ -34,7 +34,7 @@ struct DeviceGuard {
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 #ifndef SMDD_TC_ADJ_TMA
-#define SMDD_TC_ADJ_TMA 1   // the split-BF16 adjoint without reciprocity writes its tiles by tensor-map stores
+#define SMDD_TC_ADJ_TMA 1   // the split-BF16 adjoint writes its single-written tiles by tensor-map stores
 #endif
 
 }  // namespace

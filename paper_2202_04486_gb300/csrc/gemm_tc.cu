@@ -547,10 +547,11 @@ __device__ __forceinline__ void tc_adj_body(const GemmArgs &a, int bx, int by, u
     // after a timeout, give products still in flight one more bounded wait before TMEM is freed
     if (!ok && issued) mbar_wait_bounded(&bar, phase & 1);
     tc_fence_after();
-    if constexpr (!RECIP && TMA) {
-        // epilogue by the tensor memory accelerator, in two passes of 64 columns: TMEM -> four staged
-        // boxes of 16 complex x 128 rows (128-byte swizzle: granule g of row m at g ^ (m % 8)) -> four tiled
-        // stores of the tensor map of C (clipped at nv and nr)
+    // epilogue by the tensor memory accelerator for a tile written once (no reciprocity, or an off-diagonal
+    // tile of a symmetric model's adjoint, whose mirror is not needed), in two passes of 64 columns: TMEM ->
+    // four staged boxes of 16 complex x 128 rows (128-byte swizzle: granule g of row m at g ^ (m % 8)) ->
+    // four tiled stores of the tensor map of C (clipped at nv and nr)
+    if (TMA && (!RECIP || (a.no_mirror && vb != rb))) {
         for (int pass = 0; pass < 2; ++pass) {
             if (ok) {
                 const int q = warp & 3, hc = warp >> 2;   // lanes 32q.., columns 32hc.. of this pass
@@ -655,6 +656,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj(GemmArgs a) {
 template <bool IMG = false>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj_tma(GemmArgs a, const __grid_constant__ CUtensorMap tmap) {
     tc_adj_body<false, false, true, IMG>(a, blockIdx.x, blockIdx.y, 0, &tmap);
+}
+
+// the adjoint of a symmetric model (reciprocity, a.no_mirror): off-diagonal tiles written by the tensor memory
+// accelerator, diagonal tiles with their mirror by the threads
+template <bool IMG = false>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_adj_sym_tma(GemmArgs a, const __grid_constant__ CUtensorMap tmap) {
+    tc_adj_body<true, false, true, IMG>(a, blockIdx.x, blockIdx.y, 0, &tmap);
 }
 
 // work-queue form: tile t of a problem is (bx, by) = (t % tiles, t / tiles) with tiles the output tiles
@@ -925,6 +933,8 @@ cudaError_t tc_prepare() {
     if ((e = cudaFuncSetAttribute(k_tc_adj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_adj_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_sym_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_adj_sym_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdj::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<16, 1>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<32, 1>::SMEM))) return e;
     if ((e = cudaFuncSetAttribute(k_tc_fwd_q<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwd<64, 1>::SMEM))) return e;
@@ -1022,7 +1032,13 @@ cudaError_t launch_tc_adj(const GemmArgs &a0, bool recip, int nf, cudaStream_t s
     a.tiles_v = (a.nv + 127) / 128;
     a.tiles_r = (a.nr + 127) / 128;
     const bool img = a.img != nullptr;
-    if (recip) {
+    if (recip && map && a.no_mirror) {
+        CUtensorMap tmap;
+        memcpy(&tmap, map, sizeof(tmap));
+        const dim3 grid(a.tiles_v * (a.tiles_v + 1) / 2, nf);
+        if (img) k_tc_adj_sym_tma<true><<<grid, TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
+        else k_tc_adj_sym_tma<false><<<grid, TC_THREADS, TcAdj::SMEM, st>>>(a, tmap);
+    } else if (recip) {
         if (img) k_tc_adj<true, true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
         else k_tc_adj<true><<<dim3(a.tiles_v * (a.tiles_v + 1) / 2, nf), TC_THREADS, TcAdj::SMEM, st>>>(a);
     } else if (map) {
