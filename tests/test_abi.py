@@ -100,3 +100,13 @@ def test_forward_static_requires_status_word(lib):
     import ctypes
     p = ctypes.c_void_p(256)   # never dereferenced: the argument check comes first
     assert lib.mdc_forward_static(8, 2, 2, 2, 1.0, p, p, p, 1, p, None, None) == binding.MDC_ERR_INVALID_ARG
+
+
+def test_profile_driver_fails_loudly_without_cuda():
+    """The profiling driver runs the library's steps only: without a GPU it raises instead of falling back."""
+    import torch
+    from paper_2202_04486_gb300 import profile_step
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        profile_step.main(["--nt", "8", "--nr", "4", "--nv", "4", "--ns", "4", "--nb", "2"])
