@@ -112,9 +112,10 @@ int mdc_adjoint(mdc_plan_t plan, const float *R, const int32_t *idx, int nb, flo
                                    same X pointer (the caller promises X was not modified in between;
                                    ignored if the plan holds no spectrum for this pointer) */
 #define SMDD_UOBS_GATHERED  8   /* U_obs is [nb][nv][nt]: the batch rows, already gathered */
-#define SMDD_SYMMETRIC      64  /* with SMDD_RECIPROCITY (smdd_step, smdd_step_host, batched epochs): the caller
-                                   promises X[v][r] == X[r][v] on entry -- a symmetric start stays symmetric
-                                   under C_r (Eq. 4, X = C_r z) -- so the update transforms only the traces on
+#define SMDD_SYMMETRIC      64  /* with SMDD_RECIPROCITY (smdd_step, smdd_step_host, smdd_step_ex, batched epochs):
+                                   the caller promises X[v][r] == X[r][v] on entry, and the same of the N-SGD
+                                   velocity or the Adam moments (zero starts) -- a symmetric start stays
+                                   symmetric under C_r (Eq. 4, X = C_r z) -- so the update transforms only the traces on
                                    and above the diagonal (in blocks of the FFT kernels' traces per CTA) and
                                    writes each result to both (v, r) and (r, v); the result is identical to the
                                    step without the flag on a symmetric X.  On a non-symmetric X the lower

@@ -646,7 +646,7 @@ int step_impl(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx, in
     const int v_upd = ext ? 0 : ((recip && (flags & SMDD_SYMMETRIC) && v_plan == 2) ? 0 : v_plan);
     p->fft_variant = v_upd;
     const TraceGrid mg = model_grid(p, p->nv);
-    const bool sym = recip && (flags & SMDD_SYMMETRIC) && !ext && (1 << mg.ti_log2) == traces_per_cta(p) &&
+    const bool sym = recip && (flags & SMDD_SYMMETRIC) && (1 << mg.ti_log2) == traces_per_cta(p) &&
                      traces_per_cta(p) <= 32;
     const int tr_upd = traces_per_cta(p);
     p->fft_variant = v_plan;
@@ -868,7 +868,8 @@ int smdd_step_ex(mdc_plan_t p, float *X, const float *U_obs, const int32_t *idx,
     if (rc) return rc;
     if (!prm) return MDC_ERR_INVALID_ARG;
     const int flags = prm->flags;
-    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_NESTEROV | SMDD_ADAM))
+    if (flags & ~(SMDD_RECIPROCITY | SMDD_KEEP_XHAT | SMDD_REUSE_XHAT | SMDD_UOBS_GATHERED | SMDD_NESTEROV | SMDD_ADAM |
+                  SMDD_SYMMETRIC))
         return MDC_ERR_INVALID_ARG;
     if (prm->reserved != 0) return MDC_ERR_INVALID_ARG;
     if (!std::isfinite(prm->alpha)) return MDC_ERR_INVALID_ARG;

@@ -137,7 +137,7 @@ cudaError_t launch_residual(int M, const FftArgs &a, int nblocks_expected, cudaS
 
 cudaError_t launch_update(int M, bool keep, const FftArgs &a, cudaStream_t st) {
     const bool ext = a.vel || a.mute || a.adam_m;
-    if (a.g.sym && (ext || a.variant == 2)) return cudaErrorInvalidValue;   // the upper enumeration: SGD, radix plans
+    if (a.g.sym && a.variant == 2) return cudaErrorInvalidValue;   // the upper enumeration: radix plans
     if (a.variant == 2 && !ext) return launch2_update(M, keep, a, st);
     SMDD_SWITCH_M(M, { return FftLaunch<MM>::update(keep, a, st); });
     return cudaSuccess;

@@ -421,21 +421,22 @@ __global__ void __launch_bounds__(Team<M>::THREADS, Team<M>::MINB) k_residual(Ff
 // momentum (see the else branch);  optionally Gh <- rfft(X_new) (in place).
 // Trace grid: i = receiver r, j = virtual source v (model layout [nv][nr][nt]).
 //
-// Symmetric model (a.g.sym, reciprocity on a square grid with X[v][r] = X[r][v]): only the tiles on or above
-// the TR-block diagonal run; a trace (v, r) of a tile above it (r >= TR (v / TR + 1)) also writes its
-// mirror X[r][v], which it equals, and the spectra below the block diagonal are left to
-// launch_mirror_lower.  Traces of the diagonal blocks run in both orders (their mirrors are in the same
+// Symmetric model (a.g.sym, reciprocity on a square grid with X[v][r] = X[r][v], and so the velocity or the
+// moments of a symmetric start): only the tiles on or above the TR-block diagonal run; a trace (v, r) of a
+// tile above it (r >= TR (v / TR + 1)) also writes its mirror (r, v) of each array, which it equals, and the
+// spectra below the block diagonal are left to launch_mirror_lower or to the transposed read of the
+// forward product.  Traces of the diagonal blocks run in both orders (their mirrors are in the same
 // block row and column), so every element of X is written once.
 template <int M, int V, bool KEEP, bool EXT>
 __device__ __forceinline__ void update_body(const FftArgs &a, int bid_in) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int T = Team<M>::T, R = fft_radix(M, 0, V), QQ = FFT_P / R / 2, S = M / R;
     const int tr = threadIdx.x / T, t = threadIdx.x % T;
-    const int bid = (!EXT && a.g.sym) ? sym_tile_to_full(a.g, Team<M>::TR, bid_in) : bid_in;
+    const int bid = a.g.sym ? sym_tile_to_full(a.g, Team<M>::TR, bid_in) : bid_in;
     const TileCoord c = coord_of<M>(a.g, tr, bid);
     float *x = a.tout + (c.valid ? (long long)c.i * a.g.tsi + (long long)c.j * a.g.tsj : 0);
     // the mirror trace (r, v) of a trace above the block diagonal
-    float *xm = (!EXT && a.g.sym && c.valid && c.i / Team<M>::TR > c.j / Team<M>::TR)
+    float *xm = (a.g.sym && c.valid && c.i / Team<M>::TR > c.j / Team<M>::TR)
                     ? a.tout + (long long)c.j * a.g.tsi + (long long)c.i * a.g.tsj
                     : nullptr;
 
@@ -513,6 +514,15 @@ __device__ __forceinline__ void update_body(const FftArgs &a, int bid_in) {
                 if (mp) {
                     store_quad(mp, i0, a.nt, a.vec, make_float4(mk[0], mk[1], mk[2], mk[3]));
                     store_quad(sp, i0, a.nt, a.vec, make_float4(sk[0], sk[1], sk[2], sk[3]));
+                }
+                if (xm) {   // the mirror trace of a symmetric model, and of its velocity or moments
+                    const long long moff = xm - a.tout;
+                    store_quad(xm, i0, a.nt, a.vec, z);
+                    if (vp) store_quad(a.vel + moff, i0, a.nt, a.vec, make_float4(vk[0], vk[1], vk[2], vk[3]));
+                    if (mp) {
+                        store_quad(a.adam_m + moff, i0, a.nt, a.vec, make_float4(mk[0], mk[1], mk[2], mk[3]));
+                        store_quad(a.adam_v + moff, i0, a.nt, a.vec, make_float4(sk[0], sk[1], sk[2], sk[3]));
+                    }
                 }
                 xo[hs] = z;
             }

@@ -150,7 +150,7 @@ def test_step_ex_host_errors():
         dict(flags=0, V=V, mu=0.5),                                  # a velocity without the flag
         dict(flags=binding.SMDD_NESTEROV, V=V, mu=1.0),              # mu out of range
         dict(flags=binding.SMDD_NESTEROV, V=X, mu=0.5),              # V aliases X
-        dict(flags=64, V=None, mu=0.0),                              # unknown flag
+        dict(flags=128, V=None, mu=0.0),                             # unknown flag
     ]
     for c in cases:
         with pytest.raises(binding.MDCError) as e:

@@ -103,7 +103,7 @@ def test_symmetric_step_matches_oracle(shape):
     plan.close()
 
 
-def test_symmetric_flag_ignored_without_reciprocity_and_with_momentum():
+def test_symmetric_flag_ignored_without_reciprocity():
     nt, n, ns, nb = 128, 20, 10, 4
     D, X, U = _problem(nt, n, ns, seed=11)
     plan = binding.MDCPlan(_cuda(D), n, nb_max=nb)
@@ -112,11 +112,38 @@ def test_symmetric_flag_ignored_without_reciprocity_and_with_momentum():
     plan.step(Xa, _cuda(U), idx, 1e-3, 0)
     plan.step(Xb, _cuda(U), idx, 1e-3, binding.SMDD_SYMMETRIC)
     assert torch.equal(Xa, Xb)
-    # N-SGD: the momentum update runs on every trace (the flag is not accepted by smdd_step_ex)
-    with pytest.raises(binding.MDCError):
-        binding.smdd_step_ex(plan.handle, Xb, _cuda(U), idx, 1e-3,
-                             binding.SMDD_RECIPROCITY | binding.SMDD_SYMMETRIC | binding.SMDD_NESTEROV,
-                             V=torch.zeros_like(Xb), mu=0.5)
+    plan.close()
+
+
+@pytest.mark.parametrize("solver", ["nsgd", "adam"])
+@pytest.mark.parametrize("shape", [(512, 70, 40, 16), (1500, 45, 20, 7)], ids=lambda s: "x".join(map(str, s)))
+def test_symmetric_momentum_and_adam_bit_identical(shape, solver):
+    """N-SGD (velocity) and Adam (moments) with the causality mute on a symmetric model: the flagged steps
+    mirror the state arrays too, and give the bits of the unflagged steps (X and the state, three steps)."""
+    nt, n, ns, nb = shape
+    D, X, U = _problem(nt, n, ns, seed=nt + 7)
+    mute = _cuda(synth.direct_arrival_mute(n, n, nt), torch.int32)
+    rng = np.random.default_rng(4)
+    batches = [rng.permutation(ns)[:nb].astype(np.int32) for _ in range(3)]
+    plan = binding.MDCPlan(_cuda(D), n, nb_max=nb)
+    alpha = 0.2 / plan.sigma2_max(30)
+    outs = []
+    for sym in (False, True):
+        Xg, Ug = _cuda(X), _cuda(U)
+        A, B = torch.zeros_like(Xg), torch.zeros_like(Xg)
+        for k, b in enumerate(batches):
+            fl = binding.SMDD_RECIPROCITY | binding.SMDD_KEEP_XHAT | (binding.SMDD_REUSE_XHAT if k else 0)
+            fl |= binding.SMDD_SYMMETRIC if sym else 0
+            ib = _cuda(b, torch.int32)
+            if solver == "nsgd":
+                plan.step_nsgd(Xg, A, Ug, ib, alpha, mu=0.9, flags=fl, mute=mute)
+            else:
+                plan.step_adam(Xg, A, B, Ug, ib, 1e-3, k + 1, flags=fl, mute=mute)
+        assert plan.sync_status() == binding.MDC_OK
+        outs.append([t.cpu().numpy() for t in (Xg, A, B)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert np.array_equal(outs[1][0], outs[1][0].transpose(1, 0, 2))
     plan.close()
 
 
