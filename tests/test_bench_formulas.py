@@ -43,3 +43,22 @@ def test_update_bytes_per_launch_by_hand():
     assert w["bytes"] == 201 * 201 * 512 * 4 * 2 == 165482496
     assert w["staged"] == 201 * 201 * 513 * 8 * 2
     assert w["flops"] == 2 * 2.5 * 1024 * 10 * 201 * 201
+
+
+def test_symmetric_model_work_by_hand():
+    # nt 512, 201 x 201 with reciprocity and a symmetric model: 201 * 202 / 2 = 20301 distinct traces carry the
+    # model FFTs; the model is read on them and written whole; the symmetric gradient is formed in the adjoint
+    # product, so there is no gradient round trip
+    nt, n, nb = 512, 201, 16
+    up = 201 * 202 // 2
+    assert bench.model_traces(n, n, True) == up == 20301
+    fg, ff = bench.step_work(nt, n, n, nb, sym=True)
+    assert fg == 16.0 * nb * n * n * 513
+    assert ff == 2 * 2.5 * 1024 * 10 * (up + nb * n)
+    assert bench.step_bytes_compulsory(nt, n, n, nb, True, sym=True) == (up + n * n) * nt * 4 + 513 * nb * n * 8 + nb * n * nt * 4
+    w = bench.kernel_work("update", nt, n, n, nb, sym=True)
+    assert w["bytes"] == (up + n * n) * nt * 4
+    assert w["flops"] == 2 * 2.5 * 1024 * 10 * up
+    assert w["staged"] == 2 * up * 513 * 8
+    # without the flag nothing changes
+    assert bench.step_work(nt, n, n, nb) == (16.0 * nb * n * n * 513, 2 * 2.5 * 1024 * 10 * (n * n + nb * n))
