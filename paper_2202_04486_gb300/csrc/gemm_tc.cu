@@ -8,9 +8,10 @@
 // descriptor.  So each K-step of 16 issues 12 MMAs of M = 128 rows into two accumulators (re, im).
 //
 // The CUDA threads of a CTA load the FP32 complex spectra (coalesced rows), split them and store the
-// four BF16 planes (re hi, re lo, im hi, im lo) in the 128-byte swizzled layouts of tc_common.cuh;
-// thread 0 issues the MMAs and commits them to an mbarrier; every wait is bounded.  Status bits:
-// 1 = a source index out of range, 2 = a bounded wait gave up.
+// four BF16 planes (re hi, re lo, im hi, im lo) in the 128-byte swizzled layouts of tc_common.cuh -- or,
+// for the adjoint of a plan that holds them, copy the planes from operand images split once per step
+// (k_tc_adj_images); thread 0 issues the MMAs and commits them to an mbarrier; every wait is bounded.
+// Status bits: 1 = a source index out of range, 2 = a bounded wait gave up.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>

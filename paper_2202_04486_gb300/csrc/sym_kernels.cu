@@ -1,7 +1,8 @@
 // Spectra of a symmetric model (reciprocity, Eq. 4: X = C_r z with C_r = (I + T) / 2 keeps X[v][r] = X[r][v]
 // from a symmetric start).  The update of such a model transforms only the traces on and above the
-// TR-block diagonal (fft_kernels.cuh); the forward products of the next step read whole rows of the model
-// spectra, so the part below the block diagonal is filled here by a transposed copy, per frequency bin:
+// TR-block diagonal (fft_kernels.cuh).  The forward product of the next step reads whole rows of the model
+// spectra: the split-BF16 tile kernel reads the part below the block diagonal transposed, and for any
+// other product kernel that part is filled here first by a transposed copy, per frequency bin:
 //   X^[f][v][r] = X^[f][r][v]   for r < TR floor(v / TR).
 // Tiles of 32 x 32 bins below (or on) the 32-block diagonal go through shared memory, read and written
 // as rows of 256 bytes.
