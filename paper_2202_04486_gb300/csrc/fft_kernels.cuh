@@ -52,7 +52,7 @@ __device__ __forceinline__ TileCoord coord_of(const TraceGrid &g, int tr, int bi
 // Upper enumeration of a square grid (TraceGrid::sym): tile number bid -> the number of the same tile in
 // the full enumeration (bi + nbi j).  Rows j = TR g .. TR g + TR - 1 form group g, each row holding the
 // tiles bi = g .. nbi - 1, so group g starts at G(g) = TR (g nbi - g (g - 1) / 2).
-__device__ __forceinline__ int sym_tile_to_full(const TraceGrid &g, int TR, int bid) {
+__host__ __device__ __forceinline__ int sym_tile_to_full(const TraceGrid &g, int TR, int bid) {
     const int nbi = (g.ni + TR - 1) / TR;
     auto G = [&](long long q) { return (long long)TR * (q * nbi - q * (q - 1) / 2); };
     const float h = nbi + 0.5f;
