@@ -11,7 +11,9 @@ graph.  Single problems: --workload smdd_nt512_n201_nb16_recip etc.
 Prints one JSON line (rank 0).  `value` is the algorithmic FLOP rate of the whole job: per SGD step
     F_gemm = 16 nb nr nv nf                      (forward + adjoint complex products, 8 real flops / MAC)
     F_fft  = 5 N log2(N) (nr nv + nb nv)         (two real FFTs per model trace and per residual trace,
-                                                  2.5 N log2 N flops each)
+                                                  2.5 N log2 N flops each; with reciprocity the model is
+                                                  symmetric and nr nv becomes its nv (nv + 1) / 2 distinct
+                                                  traces, the step the library runs)
 with N the smallest 2^a 3^b 5^c >= 2 nt - 1 and nf = N/2 + 1 (the shortest transform that keeps the
 linear convolution exact, whatever length the library pads to), summed over the steps of all ranks and
 divided by the max over ranks of the device time.  The roofline figures divide the same algorithmic work
