@@ -110,3 +110,17 @@ def test_profile_driver_fails_loudly_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         profile_step.main(["--nt", "8", "--nr", "4", "--nv", "4", "--ns", "4", "--nb", "2"])
+
+
+def test_binding_constants_equal_the_header():
+    """Every status, flag, precision, product-kernel and batch-layout constant the binding passes to the
+    library has the value include/smdd.h gives it."""
+    text = open(os.path.join(ROOT, "include", "smdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+((?:MDC|SMDD)_[A-Z0-9_]+)\s+(\d+)", text)}
+    values.update({m.group(1): int(m.group(2)) for m in re.finditer(r"\b((?:MDC)_[A-Z0-9_]+)\s*=\s*(\d+)", text)})
+    names = [n for n in dir(binding) if re.fullmatch(r"(MDC|SMDD)_[A-Z0-9_]+", n)]
+    assert len(names) >= 20
+    for n in names:
+        assert n in values, f"{n} is not declared in include/smdd.h"
+        assert getattr(binding, n) == values[n], n
